@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs (cells, parameters, orbitals) for the TC operator.
+
+This module holds input recipes only -- no step of the operator itself.  The
+caller supplies the plane-wave basis (Miller vectors and k+G per k-point); the
+module draws coefficients on it.  Seeds are 230207420 + workload index.
+
+Workloads (all in Hartree atomic units):
+
+* ``heg_14``   -- homogeneous electron gas, simple-cubic cell, N = 14 electrons
+  (7 doubly occupied plane waves n in {0, +-e_x, +-e_y, +-e_z}), r_s = 4,
+  Gamma only, FFT box 16^3, sphere |n|^2 <= 16; chi = phi.
+* ``si_k444``  -- silicon-like FCC cell, a = 10.26 bohr, 8 electrons (4 occupied
+  bands per k), 4x4x4 Gamma-centred mesh, ecut = 7.5 Ha (15 Ry), box 24^3.
+  Coefficients (N(0,1) + i N(0,1))/sqrt(2) exp(-|k+G|^2/4), QR-orthonormalised per
+  k; chi = X' (Phi^H X')^{-1} with X' = Phi + 1e-2 R (R drawn the same way,
+  column-normalised), so chi^H phi = I and <phi_i|phi_i> = 1.
+* ``heg_114``  -- HEG, N = 114 electrons (57 plane waves, |n|^2 <= 5), r_s = 2,
+  Gamma only, box 48^3, sphere |n|^2 <= 144.
+* ``tiny_*``   -- small random cells for brute-force checks.
+
+Jastrow parameters follow Eqs. A_normalize and cusp: A = sqrt(Omega/(4 pi N)),
+C_pp = sqrt(2 A), C_ap = sqrt(A).
+"""
+import numpy as np
+
+SEED0 = 230207420
+
+
+def jastrow_params(Omega, nelec, A=None):
+    if A is None:
+        A = np.sqrt(Omega / (4.0 * np.pi * nelec))
+    return [A, A], [np.sqrt(2.0 * A), np.sqrt(A)]
+
+
+def heg_params(nelec, rs, fft, radius2):
+    L = (nelec * 4.0 * np.pi / 3.0) ** (1.0 / 3.0) * rs
+    lattice = np.eye(3) * L
+    Omega = L ** 3
+    b = 2.0 * np.pi / L
+    ecut = 0.5 * radius2 * b * b * (1.0 + 1e-9)
+    A, C = jastrow_params(Omega, nelec)
+    nocc = nelec // 2
+    return dict(lattice=lattice, kmesh=(1, 1, 1), ecut=ecut, fft=(fft,) * 3, nbands=nocc,
+                nocc=nocc, A=A, C=C, nelec=nelec)
+
+
+def si_params(kmesh=(4, 4, 4), fft=24, ecut=7.5, nbands=4, nocc=4):
+    a = 10.26
+    lattice = 0.5 * a * np.array([[0.0, 1.0, 1.0], [1.0, 0.0, 1.0], [1.0, 1.0, 0.0]])
+    Omega = abs(np.linalg.det(lattice))
+    A, C = jastrow_params(Omega, 8)
+    return dict(lattice=lattice, kmesh=tuple(kmesh), ecut=ecut, fft=(fft,) * 3, nbands=nbands,
+                nocc=nocc, A=A, C=C, nelec=8)
+
+
+def tiny_params(seed, kmesh=(1, 1, 2), fft=(8, 9, 10), ecut=1.2, nbands=3, nocc=2, scale=6.0):
+    """A slightly distorted triclinic cell, for brute-force and invariance checks."""
+    rng = np.random.default_rng(SEED0 + 100 + seed)
+    lattice = scale * (np.eye(3) + 0.15 * rng.standard_normal((3, 3)))
+    Omega = abs(np.linalg.det(lattice))
+    A, C = jastrow_params(Omega, 2 * nocc)
+    return dict(lattice=lattice, kmesh=tuple(kmesh), ecut=ecut, fft=tuple(fft), nbands=nbands,
+                nocc=nocc, A=A, C=C, nelec=2 * nocc)
+
+
+WORKLOADS = {
+    "heg_14": lambda: heg_params(14, 4.0, 16, 16),
+    "si_k444": lambda: si_params(),
+    "heg_114": lambda: heg_params(114, 2.0, 48, 144),
+}
+
+
+def _gauss_coeffs(rng, kpg, npw_max, nbands):
+    npw = kpg.shape[0]
+    damp = np.exp(-np.einsum("ij,ij->i", kpg, kpg) / 4.0)
+    c = (rng.standard_normal((npw, nbands)) + 1j * rng.standard_normal((npw, nbands))) / np.sqrt(2.0)
+    return c * damp[:, None]
+
+
+def random_orbitals(seed, kpg_list, npw_max, nbands, perturb=1e-2):
+    """(c_phi, c_chi) of shape (Nk, nbands, npw_max), biorthonormal per k.
+
+    ``kpg_list[k]`` is the (npw_k, 3) array of Cartesian k+G of the sphere at k.
+    """
+    rng = np.random.default_rng(seed)
+    Nk = len(kpg_list)
+    c_phi = np.zeros((Nk, nbands, npw_max), dtype=np.complex128)
+    c_chi = np.zeros_like(c_phi)
+    for k, kpg in enumerate(kpg_list):
+        npw = kpg.shape[0]
+        P = _gauss_coeffs(rng, kpg, npw_max, nbands)
+        P, _ = np.linalg.qr(P)
+        R = _gauss_coeffs(rng, kpg, npw_max, nbands)
+        R = R / np.linalg.norm(R, axis=0, keepdims=True)
+        Xp = P + perturb * R
+        X = Xp @ np.linalg.inv(P.conj().T @ Xp)
+        c_phi[k, :, :npw] = P.T
+        c_chi[k, :, :npw] = X.T
+    return c_phi, c_chi
+
+
+def heg_orbitals(miller0, npw_max, radius2_occ):
+    """Unit plane waves on all Miller vectors with |n|^2 <= radius2_occ (Gamma only).
+
+    Orbitals are ordered by (|n|^2, n1, n2, n3); returns c (1, nocc, npw_max).
+    """
+    m = np.asarray(miller0)
+    r2 = np.einsum("ij,ij->i", m, m)
+    sel = np.nonzero(r2 <= radius2_occ)[0]
+    order = sorted(sel, key=lambda i: (r2[i], m[i, 0], m[i, 1], m[i, 2]))
+    c = np.zeros((1, len(order), npw_max), dtype=np.complex128)
+    for b, i in enumerate(order):
+        c[0, b, i] = 1.0
+    return c
+
+
+def occupations(Nk, nbands, nocc, fill=1.0):
+    occ = np.zeros((Nk, nbands))
+    occ[:, :nocc] = fill
+    return occ

@@ -1,0 +1,62 @@
+"""Pins of the oracle's basis and divergence-correction constant (Sec. 2.6)."""
+import numpy as np
+import pytest
+
+from conftest import make_setup
+from oracle import cell as CL
+from oracle import ewald
+from paper_2302_07420_gb300 import synth
+
+# Madelung constant of the simple-cubic lattice of unit charges in a neutralising
+# background: v_M L = -2.837297479480620 (standard value, e.g. Nijboer & De Wette 1957).
+SC_MADELUNG = 2.837297479480620
+
+
+def test_simple_cubic_madelung_constant():
+    for L in (1.0, 15.54052, 7.67663317071):
+        g0 = CL.gamma0(np.eye(3) * L, (1, 1, 1), CL.default_alpha(np.eye(3) * L, (1, 1, 1)))
+        cC = 4 * np.pi * g0 / L ** 3
+        assert abs(cC * L - SC_MADELUNG) < 2e-12
+
+
+@pytest.mark.parametrize("kmesh", [(1, 1, 1), (2, 2, 2), (4, 4, 4), (1, 2, 3)])
+def test_correction_constant_is_minus_supercell_madelung(kmesh):
+    p = synth.si_params(kmesh=kmesh)
+    lat = p["lattice"]
+    Om = abs(np.linalg.det(lat))
+    g0 = CL.gamma0(lat, kmesh, CL.default_alpha(lat, kmesh))
+    vM = ewald.madelung(lat * np.asarray(kmesh)[:, None])
+    assert abs(4 * np.pi * g0 / Om + vM) < 1e-10 * abs(vM)
+
+
+def test_triclinic_and_alpha_insensitivity():
+    p = synth.tiny_params(0)
+    lat, km = p["lattice"], (2, 1, 3)
+    Om = abs(np.linalg.det(lat))
+    a0 = CL.default_alpha(lat, km)
+    c1 = 4 * np.pi * CL.gamma0(lat, km, a0) / Om
+    c2 = 4 * np.pi * CL.gamma0(lat, km, a0 * (12 / 14) ** 2) / Om
+    assert abs(c1 - c2) < 1e-10 * abs(c1)
+    assert abs(c1 + ewald.madelung(lat * np.asarray(km)[:, None])) < 1e-10 * abs(c1)
+
+
+def test_sphere_counts_and_order():
+    # |n|^2 <= 16 holds 257 integer vectors (Gauss lattice-point count for r^2 = 16)
+    S = make_setup(synth.heg_params(14, 4.0, 16, 16))
+    assert S.npw.tolist() == [257]
+    m = S.miller[0]
+    assert all(tuple(m[i]) < tuple(m[i + 1]) for i in range(len(m) - 1))
+    # |n|^2 <= 5 holds 57 vectors (1 + 6 + 12 + 8 + 6 + 24)
+    S = make_setup(synth.heg_params(114, 2.0, 48, 144))
+    assert int(np.sum(np.einsum("ij,ij->i", S.miller[0], S.miller[0]) <= 5)) == 57
+    # the sphere is invariant under k -> k + G: counts depend only on the k-point class
+    S = make_setup(synth.si_params())
+    assert S.npw.sum() == sum(len(CL.sphere_miller(S.kcart[k] + S.B[0], S.B, S.ecut)) for k in range(S.Nk))
+
+
+def test_kmesh_and_box_conventions():
+    f = CL.kmesh_frac((4, 1, 3))
+    assert f.shape == (12, 3)
+    assert np.all(f > -0.5) and np.all(f <= 0.5)
+    assert CL.fft_rep(6).tolist() == [0, 1, 2, -3, -2, -1]
+    assert CL.fft_rep(5).tolist() == [0, 1, 2, -2, -1]
