@@ -1,0 +1,146 @@
+/*
+ * tc.h -- C ABI of the GB300 transcorrelated (TC / BITC) interaction operator.
+ *
+ * The library applies the effective two-body and three-body interactions of
+ * the TC Hamiltonian (M. Ochi, arXiv:2302.07420, Sec. 2.1, Eqs. V2body and
+ * V3body; the three-body part contracted over occupied orbitals as in
+ * Eq. SCF / Eq. BITCSCF) to every right orbital phi and every left orbital chi
+ * at every k-point, including the divergence corrections for k-points on the
+ * SCF mesh (Sec. 2.6 and the corrections listed in Sec. 2.7.4).  One spin
+ * channel is computed (non-spin-polarised: both channels hold the same
+ * orbitals); same-spin pairs use the parallel-spin Jastrow (A[0], C[0]) and
+ * opposite-spin pairs the antiparallel one (A[1], C[1]).
+ *
+ * Units: Hartree atomic units.  Orbitals are given by their plane-wave
+ * coefficients c(G) on the sphere |k+G|^2/2 <= ecut_ha, normalised so that
+ * sum_G |c(G)|^2 = 1 (phi_periodic(r) = sum_G c(G) e^{iG.r} / sqrt(Omega),
+ * Sec. 2.4).  Outputs are coefficients in the same units on the same sphere.
+ *
+ * Layout of every orbital array: interleaved complex FP64
+ * [Nk][nbands][npw_max] (real, imaginary), zero padded beyond npw(k), in the
+ * k and G order reported by tc_layout: k index (i1*N2 + i2)*N3 + i3 of the
+ * Gamma-centred mesh with fractional coordinates in (-1/2, 1/2]; G order
+ * lexicographic in the Miller indices (m1, m2, m3).
+ *
+ * Pointers: orbital arrays may be device pointers or host pointers (pageable
+ * or pinned); host arrays are staged through the library's own device buffers
+ * on the given stream, so a call with host pointers includes the copies and
+ * returns after the outputs have landed.  occ is always a host array.
+ *
+ * Ownership: the caller owns every buffer it passes.  The context owns its
+ * tables and workspace, all allocated in tc_init; tc_apply / tc_energy
+ * allocate nothing.
+ *
+ * Errors: no call aborts or throws across the ABI.  On a non-OK status the
+ * contents of the output arrays are undefined; tc_last_error gives the reason.
+ * Threads: a context is not thread-safe; distinct contexts are independent.
+ * Streams: work is enqueued on the CUDA stream passed (cudaStream_t, NULL =
+ * legacy default stream).  Calls with device pointers return without
+ * synchronising (except tc_energy, which returns host scalars).
+ */
+#ifndef TC_GB300_H
+#define TC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_ERR_ARG = 1,          /* invalid argument (null pointer, bad size, bad parameter) */
+  TC_ERR_STATE = 2,        /* context not initialised or already destroyed */
+  TC_ERR_OOM = 3,          /* device or host allocation failed (tc_init only) */
+  TC_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+  TC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  TC_ERR_UNSUPPORTED = 6   /* valid but not supported (e.g. FFT box size) */
+} tc_status;
+
+enum { TC_FP64 = 0, TC_FP32 = 1 };
+
+/* Term indices of the operator (Sec. 2.7.3-2.7.4) and of E_terms.  The
+ * three-body outputs include their multiplicities: 3a3 and 3a4 twice (3a6 = 3a3,
+ * 3a5 = 3a4), every 3b term twice (3c = 3b). */
+enum {
+  TC_TERM_2AH = 0, TC_TERM_2BH1, TC_TERM_2BH2, TC_TERM_2AX, TC_TERM_2BX1, TC_TERM_2BX2,
+  TC_TERM_3A1, TC_TERM_3A2, TC_TERM_3A3, TC_TERM_3A4,
+  TC_TERM_3B1, TC_TERM_3B2, TC_TERM_3B3, TC_TERM_3B4, TC_TERM_3B5, TC_TERM_3B6,
+  TC_NTERMS_OP,                 /* 16 operator terms */
+  TC_TERM_KIN = TC_NTERMS_OP,   /* kinetic energy (energy breakdown only) */
+  TC_NTERMS                     /* 17 entries in E_terms */
+};
+
+typedef struct {
+  double lattice[3][3];   /* bohr, rows a_1, a_2, a_3 */
+  int kmesh[3];           /* Gamma-centred Monkhorst-Pack mesh */
+  double ecut_ha;         /* plane-wave sphere |k+G|^2/2 <= ecut_ha (Hartree) */
+  int fft[3];             /* FFT box; must be cubic, n in {9, 12, 15, 16, 24} */
+  int nbands;             /* bands per k (outputs) */
+  int nocc;               /* occupied bands per k (partners), 0 < nocc <= nbands */
+  double A[2];            /* Jastrow A (Eq. Jastrow) for [parallel, antiparallel] spins */
+  double C[2];            /* Jastrow C for [parallel, antiparallel] spins, > 0 */
+  double alpha;           /* auxiliary-function exponent (Eq. aux); <= 0 selects
+                             sqrt(alpha) = (shortest supercell vector) / 12 */
+  int div_correction;     /* 1: add the SCF-mesh divergence corrections (default) */
+  double ushort_factor;   /* factor on the u_short terms of Eqs. divcor_3a2_first and
+                             3b6_div_scf1; 1 reproduces the printed equations */
+  int precision;          /* TC_FP64 or TC_FP32 (FFTs and pair products) */
+  unsigned int term_mask; /* bit t enables operator term t; 0 enables all */
+} tc_params;
+
+typedef struct tc_ctx tc_ctx;
+
+/* Builds cell, k mesh, spheres, box maps, kernel tables (FP64 on the host) and
+ * allocates all device workspace on the current CUDA device. */
+tc_status tc_init(const tc_params* params, tc_ctx** out);
+
+/* Basis layout.  *npw_per_k -> [Nk] ints, *miller -> [Nk][npw_max][3] ints
+ * (zero padded); both pointers stay valid until tc_destroy.  Any output
+ * pointer may be NULL. */
+tc_status tc_layout(const tc_ctx* ctx, int* nk, int* npw_max, const int** npw_per_k, const int** miller);
+
+/* Scalars of the setup: out[0] = Omega, out[1] = alpha, out[2] = Gamma0 (the
+ * bracket of Eq. correction2), out[3] = number of distinct k - q vectors. */
+tc_status tc_setup_scalars(const tc_ctx* ctx, double out[4]);
+
+/* out_R = (h_2 + h_3) phi_j and out_L = (h_2 + h_3)^dagger chi_j for every
+ * orbital j (Eqs. BITCSCF and BITCSCFconj without the one-body terms).
+ * phi_R: right orbitals phi; phi_L: left orbitals chi; occ: host [Nk][nbands]
+ * occupations f in [0, 1] (only the first nocc bands act as partners).
+ * out_R / out_L may be NULL to skip that side. */
+tc_status tc_apply(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ,
+                   void* out_R, void* out_L, void* cuda_stream);
+
+/* TC pseudo-energy per unit cell, both spins (Eqs. EtotTC / EtotBiTC with a
+ * biorthonormal pair, single-determinant evaluation):
+ * E = (2/Nk) Re sum_{k,mu} f [<chi|T|phi> + <chi|h_2 phi>/2 + <chi|h_3 phi>/3].
+ * E_terms (nullable) receives the TC_NTERMS contributions.  Blocks the host. */
+tc_status tc_energy(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ,
+                    double* E_total, double* E_terms, void* cuda_stream);
+
+/* Batched 3D FFT of `batch` contiguous n^3 complex volumes in place on the
+ * device (precision TC_FP64: complex128, TC_FP32: complex64), sign -1
+ * (sum f e^{-2 pi i m.r/n}) or +1; unnormalised.  Exposes the library's
+ * shared-memory FFT for testing. */
+tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* cuda_stream);
+
+/* Device-time profiling of the stages of tc_apply / tc_energy.  Stage
+ * indices: 0 orbitals to real space, 1 densities and Hartree-type fields,
+ * 2 occupied-pair stage (Algs. 4, 6, 8, 11), 3 fused pair chains
+ * (Algs. 2, 5, 6, 9, 11, 12), 4 the 3b4 pass (Alg. 10), 5 local terms,
+ * corrections and sphere gather.  While enabled, each call records CUDA
+ * events between stages on its stream and waits for them at its end; times
+ * accumulate until tc_profile(ctx, 1) is called again. */
+enum { TC_NSTAGES = 6 };
+tc_status tc_profile(tc_ctx* ctx, int enable);
+/* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
+tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
+
+/* Reason of the last failure on ctx; with ctx == NULL, of the last failed
+ * tc_init on the calling thread.  The string lives until the next call. */
+const char* tc_last_error(const tc_ctx* ctx);
+tc_status tc_destroy(tc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_GB300_H */

@@ -1,0 +1,406 @@
+// C ABI of the TC operator library (see include/tc.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tc_ctx.hpp"
+#include "tc_kernels.cuh"
+
+using tc::NT;
+
+namespace {
+
+thread_local std::string g_init_err;   // reason of the last failed tc_init on this thread
+
+// Box sizes with compiled specialisations.
+#define TC_FOR_N(X) X(9) X(12) X(15) X(16) X(24)
+
+template <typename T> int dispatch_prepare(tc_ctx* c, int n) {
+#define CASE(NN) \
+  case NN: return tc::prepare_kernels<T, NN>(c);
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
+template <typename T> size_t dispatch_scratch(const tc::Setup& S, int n) {
+#define CASE(NN) \
+  case NN: return tc::scratch_needed<T, NN>(S);
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return 0;
+}
+
+template <typename T>
+int dispatch_run(tc_ctx* c, const double2* a, const double2* b, double2* oR, double2* oL, const double* tw, int ns,
+                 cudaStream_t st) {
+#define CASE(NN) \
+  case NN: return tc::run_pipeline<T, NN>(c, a, b, oR, oL, tw, ns, st);
+  switch (c->S.n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
+template <typename T> int dispatch_fft(int n, void* data, int batch, int sign, cudaStream_t st) {
+#define CASE(NN) \
+  case NN: return tc::run_fft3d<T, NN>(data, batch, sign, st);
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+tc_status fail(tc_ctx* c, tc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+tc_status cuda_fail(tc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, TC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t& err) {
+  std::vector<T> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (T)v[i];
+  void* d = nullptr;
+  err = cudaMalloc(&d, h.size() * sizeof(T) + 16);
+  if (err != cudaSuccess) return nullptr;
+  err = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return d;
+}
+
+void free_all(tc_ctx* c) {
+  void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
+                  c->d_hartU, c->d_hartUs, c->d_occ, c->d_phi, c->d_chi, c->d_gphi, c->d_gchi, c->d_side,
+                  c->d_cs, c->d_scratch, c->d_in_phi, c->d_in_chi, c->d_out_R, c->d_out_L, c->d_edot};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->h_occ) cudaFreeHost(c->h_occ);
+  if (c->h_edot) cudaFreeHost(c->h_edot);
+}
+
+// e[j] = sum_G conj(c_chi) (kin |k+G|^2/2 c_phi + out), FP64
+__global__ void k_energy_dot(const double2* __restrict__ cphi, const double2* __restrict__ cchi,
+                             const double2* __restrict__ out, const double* __restrict__ kpg, int npw_max, int nb,
+                             int kin, double2* e) {
+  __shared__ double rx[32], ry[32];
+  const int j = blockIdx.x, k = j / nb;
+  double sx = 0, sy = 0;
+  for (int g = threadIdx.x; g < npw_max; g += blockDim.x) {
+    const double2 x = cchi[(size_t)j * npw_max + g];
+    double2 v = out ? out[(size_t)j * npw_max + g] : make_double2(0.0, 0.0);
+    if (kin) {
+      const double* q = kpg + ((size_t)k * npw_max + g) * 3;
+      const double t = 0.5 * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+      const double2 p = cphi[(size_t)j * npw_max + g];
+      v.x += t * p.x;
+      v.y += t * p.y;
+    }
+    sx += x.x * v.x + x.y * v.y;   // conj(x) v
+    sy += x.x * v.y - x.y * v.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  if ((threadIdx.x & 31) == 0) { rx[threadIdx.x >> 5] = sx; ry[threadIdx.x >> 5] = sy; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ax = 0, ay = 0;
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) { ax += rx[i]; ay += ry[i]; }
+    e[j] = make_double2(ax, ay);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_init(const tc_params* params, tc_ctx** out) {
+  if (!params || !out) return TC_ERR_ARG;
+  *out = nullptr;
+  tc_ctx* c = new (std::nothrow) tc_ctx();
+  if (!c) return TC_ERR_OOM;
+  std::string why = tc::build_setup(*params, c->S);
+  g_init_err = why;
+  if (!why.empty()) {
+    const tc_status st = why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
+    delete c;
+    return st;
+  }
+  tc::Setup& S = c->S;
+  c->prec = params->precision;
+  c->esz = c->prec == TC_FP64 ? 16 : 8;
+  cudaGetDevice(&c->device);
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; return r == cudaSuccess; };
+  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb;
+  // basis
+  ok(cudaMalloc((void**)&c->d_box_index, S.box_index.size() * sizeof(int)));
+  if (e == cudaSuccess) ok(cudaMemcpy(c->d_box_index, S.box_index.data(), S.box_index.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<double> kpg((size_t)S.Nk * S.npw_max * 3, 0.0);
+  for (int k = 0; k < S.Nk; ++k)
+    for (int g = 0; g < S.npw[k]; ++g)
+      for (int d = 0; d < 3; ++d) {
+        const auto& m = S.miller[k][g];
+        kpg[((size_t)k * S.npw_max + g) * 3 + d] = S.kcart[k][d] + (m[0] * S.B[0][d] + m[1] * S.B[1][d] + m[2] * S.B[2][d]);
+      }
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_kpg, kpg.size() * sizeof(double)));
+  if (e == cudaSuccess) ok(cudaMemcpy(c->d_kpg, kpg.data(), kpg.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_delta_id, S.delta_id.size() * sizeof(int)));
+  if (e == cudaSuccess) ok(cudaMemcpy(c->d_delta_id, S.delta_id.data(), S.delta_id.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<double> dl;
+  for (auto& d : S.delta) dl.insert(dl.end(), d.begin(), d.end());
+  auto up = [&](const std::vector<double>& v) -> void* {
+    if (e != cudaSuccess) return nullptr;
+    cudaError_t r = cudaSuccess;
+    void* p = c->prec == TC_FP64 ? upload_as<double>(v, r) : upload_as<float>(v, r);
+    ok(r);
+    return p;
+  };
+  c->d_delta = up(dl);
+  c->d_tabV = up(S.tabV);
+  c->d_tabU = up(S.tabU);
+  c->d_hartV = up(S.hartV);
+  c->d_hartU = up(S.hartU);
+  c->d_hartUs = up(S.hartUs);
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_occ, nj * sizeof(double)));
+  if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_occ, nj * sizeof(double)));
+  // fields and workspace
+  const size_t vol = NN * c->esz;
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_phi, nj * vol));
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_chi, nj * vol));
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_gphi, nj * 3 * vol));
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_gchi, nj * 3 * vol));
+  const size_t side_vols = 25 + (size_t)S.Nk * S.no * 6 + nj * 4;
+  c->side_bytes = side_vols * vol;
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_side, 2 * c->side_bytes));
+  if (e == cudaSuccess) ok(cudaMemset(c->d_side, 0, 2 * c->side_bytes));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_cs, (size_t)2 * nj * S.no * 6 * sizeof(double)));
+  if (e == cudaSuccess) ok(cudaMemset(c->d_cs, 0, (size_t)2 * nj * S.no * 6 * sizeof(double)));
+  c->scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n) : dispatch_scratch<float>(S, S.n);
+  if (e == cudaSuccess) ok(cudaMalloc(&c->d_scratch, c->scratch_bytes));
+  const size_t orb = nj * S.npw_max * sizeof(double2);
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_in_phi, orb));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_in_chi, orb));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_out_R, orb));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_out_L, orb));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_edot, nj * sizeof(double2)));
+  if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_edot, nj * sizeof(double2)));
+  if (e != cudaSuccess) {
+    const tc_status st = (e == cudaErrorMemoryAllocation) ? TC_ERR_OOM : TC_ERR_CUDA;
+    g_init_err = std::string("tc_init: ") + cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return st;
+  }
+  const int r = c->prec == TC_FP64 ? dispatch_prepare<double>(c, S.n) : dispatch_prepare<float>(c, S.n);
+  if (r != TC_OK) {
+    g_init_err = c->err;
+    free_all(c);
+    delete c;
+    return (tc_status)r;
+  }
+  c->npw_host = S.npw;
+  *out = c;
+  return TC_OK;
+}
+
+tc_status tc_layout(const tc_ctx* c, int* nk, int* npw_max, const int** npw_per_k, const int** miller) {
+  if (!c) return TC_ERR_STATE;
+  if (nk) *nk = c->S.Nk;
+  if (npw_max) *npw_max = c->S.npw_max;
+  if (npw_per_k) *npw_per_k = c->npw_host.data();
+  if (miller) *miller = c->S.miller_flat.data();
+  return TC_OK;
+}
+
+tc_status tc_setup_scalars(const tc_ctx* c, double out4[4]) {
+  if (!c) return TC_ERR_STATE;
+  if (!out4) return TC_ERR_ARG;
+  out4[0] = c->S.Omega;
+  out4[1] = c->S.alpha;
+  out4[2] = c->S.Gamma0;
+  out4[3] = c->S.ndelta;
+  return TC_OK;
+}
+
+static tc_status run_common(tc_ctx* c, const void* phi, const void* chi, const double* occ, void* outR, void* outL,
+                            const double* tw, int nsides, cudaStream_t st, bool* host_out) {
+  const tc::Setup& S = c->S;
+  const size_t nj = (size_t)S.Nk * S.nb, orb = nj * S.npw_max * sizeof(double2);
+  for (size_t i = 0; i < nj; ++i) {
+    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return fail(c, TC_ERR_ARG, "occupations must lie in [0, 1]");
+    c->h_occ[i] = occ[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(c->d_occ, c->h_occ, nj * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "occ upload");
+  const double2* dphi = static_cast<const double2*>(phi);
+  const double2* dchi = static_cast<const double2*>(chi);
+  if (!is_device_ptr(phi)) {
+    e = cudaMemcpyAsync(c->d_in_phi, phi, orb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "phi_R upload");
+    dphi = c->d_in_phi;
+  }
+  if (!is_device_ptr(chi)) {
+    e = cudaMemcpyAsync(c->d_in_chi, chi, orb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "phi_L upload");
+    dchi = c->d_in_chi;
+  }
+  double2* oR = static_cast<double2*>(outR);
+  double2* oL = static_cast<double2*>(outL);
+  *host_out = false;
+  if (oR && !is_device_ptr(oR)) { oR = c->d_out_R; *host_out = true; }
+  if (oL && !is_device_ptr(oL)) { oL = c->d_out_L; *host_out = true; }
+  const int r = c->prec == TC_FP64 ? dispatch_run<double>(c, dphi, dchi, oR, oL, tw, nsides, st)
+                                   : dispatch_run<float>(c, dphi, dchi, oR, oL, tw, nsides, st);
+  if (r != TC_OK) return (tc_status)r;
+  if (outR && oR == c->d_out_R && outR != c->d_out_R) {
+    e = cudaMemcpyAsync(outR, oR, orb, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "out_R download");
+  }
+  if (outL && oL == c->d_out_L && outL != c->d_out_L) {
+    e = cudaMemcpyAsync(outL, oL, orb, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "out_L download");
+  }
+  return TC_OK;
+}
+
+static void term_weights(const tc_ctx* c, double* tw, double two, double three) {
+  const unsigned mask = c->S.prm.term_mask;
+  for (int t = 0; t < NT; ++t) {
+    const bool on = mask == 0u || (mask >> t) & 1u;
+    tw[t] = on ? (t < 6 ? two : three) : 0.0;
+  }
+}
+
+tc_status tc_apply(tc_ctx* c, const void* phi, const void* chi, const double* occ, void* outR, void* outL,
+                   void* stream) {
+  if (!c) return TC_ERR_STATE;
+  if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
+  if (!outR && !outL) return TC_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double tw[NT];
+  term_weights(c, tw, 1.0, 1.0);
+  bool host_out = false;
+  tc_status r = run_common(c, phi, chi, occ, outR, outL, tw, 2, st, &host_out);
+  if (r != TC_OK) return r;
+  if (host_out) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tc_apply");
+  }
+  return TC_OK;
+}
+
+tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* occ, double* E_total,
+                    double* E_terms, void* stream) {
+  if (!c) return TC_ERR_STATE;
+  if (!phi || !chi || !occ || !E_total) return fail(c, TC_ERR_ARG, "null pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const tc::Setup& S = c->S;
+  const int nj = S.Nk * S.nb;
+  const size_t orb = (size_t)nj * S.npw_max * sizeof(double2);
+  // device copies of the inputs (so that the dot products can read them)
+  const double2* dphi = static_cast<const double2*>(phi);
+  const double2* dchi = static_cast<const double2*>(chi);
+  cudaError_t e;
+  if (!is_device_ptr(phi)) {
+    if ((e = cudaMemcpyAsync(c->d_in_phi, phi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    dphi = c->d_in_phi;
+  }
+  if (!is_device_ptr(chi)) {
+    if ((e = cudaMemcpyAsync(c->d_in_chi, chi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    dchi = c->d_in_chi;
+  }
+  auto reduce = [&](bool kin, bool with_out, double* res) -> tc_status {
+    k_energy_dot<<<nj, 128, 0, st>>>(dphi, dchi, with_out ? c->d_out_R : nullptr, c->d_kpg, S.npw_max, S.nb, kin ? 1 : 0,
+                                     c->d_edot);
+    cudaError_t e2 = cudaGetLastError();
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "k_energy_dot");
+    e2 = cudaMemcpyAsync(c->h_edot, c->d_edot, nj * sizeof(double2), cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "energy reduction");
+    double s = 0.0;
+    for (int j = 0; j < nj; ++j) s += occ[j] * c->h_edot[j].x;
+    *res = 2.0 / S.Nk * s;
+    return TC_OK;
+  };
+  double tw[NT];
+  bool host_out = false;
+  term_weights(c, tw, 0.5, 1.0 / 3.0);
+  tc_status r = run_common(c, dphi, dchi, occ, c->d_out_R, nullptr, tw, 1, st, &host_out);
+  if (r != TC_OK) return r;
+  if ((r = reduce(true, true, E_total)) != TC_OK) return r;
+  if (E_terms) {
+    double all[NT];
+    term_weights(c, all, 0.5, 1.0 / 3.0);
+    for (int t = 0; t < NT; ++t) {
+      if (all[t] == 0.0) { E_terms[t] = 0.0; continue; }
+      double one[NT] = {0};
+      one[t] = all[t];
+      if ((r = run_common(c, dphi, dchi, occ, c->d_out_R, nullptr, one, 1, st, &host_out)) != TC_OK) return r;
+      if ((r = reduce(false, true, &E_terms[t])) != TC_OK) return r;
+    }
+    if ((r = reduce(true, false, &E_terms[TC_TERM_KIN])) != TC_OK) return r;
+  }
+  return TC_OK;
+}
+
+tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* stream) {
+  if (!data || batch < 0 || (sign != 1 && sign != -1)) return TC_ERR_ARG;
+  if (batch == 0) return TC_OK;
+  tc_ctx tmp;
+  const int pr = precision == TC_FP64 ? dispatch_prepare<double>(&tmp, n) : dispatch_prepare<float>(&tmp, n);
+  if (pr != TC_OK) return (tc_status)pr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int r = precision == TC_FP64 ? dispatch_fft<double>(n, data, batch, sign, st)
+                                     : dispatch_fft<float>(n, data, batch, sign, st);
+  return (tc_status)r;
+}
+
+tc_status tc_profile(tc_ctx* c, int enable) {
+  if (!c) return TC_ERR_STATE;
+  for (int i = 0; i < 8; ++i) {
+    c->stage_ms[i] = 0.0;
+    c->stage_launch[i] = 0;
+    if (enable && !c->ev[i]) {
+      cudaError_t e = cudaEventCreate(&c->ev[i]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "tc_profile");
+    }
+  }
+  c->profile = enable != 0;
+  return TC_OK;
+}
+
+tc_status tc_stage_times(const tc_ctx* c, double* ms, int* launches, int n) {
+  if (!c) return TC_ERR_STATE;
+  if (!ms || n < TC_NSTAGES) return TC_ERR_ARG;
+  for (int i = 0; i < TC_NSTAGES; ++i) {
+    ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_launch[i];
+  }
+  return TC_OK;
+}
+
+const char* tc_last_error(const tc_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
+
+tc_status tc_destroy(tc_ctx* c) {
+  if (!c) return TC_ERR_STATE;
+  free_all(c);
+  delete c;
+  return TC_OK;
+}
+
+}  // extern "C"

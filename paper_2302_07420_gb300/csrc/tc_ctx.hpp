@@ -1,0 +1,56 @@
+// Library context: setup, device tables and workspace (all allocated in tc_init).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "tc_setup.hpp"
+
+struct tc_ctx {
+  tc::Setup S;
+  int prec = TC_FP64;
+  size_t esz = 16;                 // bytes per complex element of the compute precision
+  std::string err;
+  int device = 0;
+  // basis
+  int* d_box_index = nullptr;      // [Nk][npw_max]
+  double* d_kpg = nullptr;         // [Nk][npw_max][3]
+  int* d_delta_id = nullptr;       // [Nk][Nk]
+  void* d_delta = nullptr;         // [ndelta][3] T
+  void* d_tabV = nullptr;          // [ndelta][2][N] T
+  void* d_tabU = nullptr;          // [ndelta][2][N] T
+  void* d_hartV = nullptr;         // [2][N] T
+  void* d_hartU = nullptr;         // [N] T
+  void* d_hartUs = nullptr;        // [2][N] T
+  double* d_occ = nullptr;         // [Nk][nb]
+  double* h_occ = nullptr;         // pinned [Nk][nb]
+  // real-space orbitals
+  void *d_phi = nullptr, *d_chi = nullptr, *d_gphi = nullptr, *d_gchi = nullptr;
+  // per side fields (2 sides), each a separate allocation block
+  void* d_side = nullptr;          // packed per-side global fields
+  size_t side_bytes = 0;
+  double* d_cs = nullptr;          // [2][Nk*nb][no][6]
+  void* d_scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // staging for host pointers and energy
+  double2 *d_in_phi = nullptr, *d_in_chi = nullptr, *d_out_R = nullptr, *d_out_L = nullptr;
+  double2* d_edot = nullptr;       // [Nk*nb]
+  double2* h_edot = nullptr;       // pinned
+  std::vector<int> npw_host;
+  // profiling (tc_profile / tc_stage_times)
+  bool profile = false;
+  cudaEvent_t ev[8] = {};
+  double stage_ms[8] = {};
+  int stage_launch[8] = {};
+};
+
+namespace tc {
+// Runs the operator pipeline on the given stream.  tw: per-term weights;
+// nsides: 2 (right and left) or 1 (right only).
+template <typename T, int N>
+int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2* outR, double2* outL,
+                 const double* tw, int nsides, cudaStream_t st);
+template <typename T, int N> int prepare_kernels(tc_ctx* ctx);
+template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cudaStream_t st);
+template <typename T, int N> size_t scratch_needed(const Setup& S);
+}  // namespace tc

@@ -1,0 +1,62 @@
+// Device-side parameter blocks of the TC operator kernels.
+#pragma once
+#include "tc_fft.cuh"
+
+namespace tc {
+
+constexpr int NT = 16;   // operator terms, order of TC_TERM_* in tc.h
+enum { T2AH, T2BH1, T2BH2, T2AX, T2BX1, T2BX2, T3A1, T3A2, T3A3, T3A4, T3B1, T3B2, T3B3, T3B4, T3B5, T3B6 };
+
+// Fields of one side.  Right side: ket = phi, bra = chi; left side: ket = chi,
+// bra = phi (Eq. BITCSCFconj).  Real-space fields are psi(r) = sum_G c(G) e^{iG.r}
+// on the unpadded n^3 grid.
+template <typename T> struct SideArgs {
+  const cplx<T>* ket;    // [Nk][nb][N]
+  const cplx<T>* bra;    // [Nk][nb][N]
+  const cplx<T>* gket;   // [Nk][nb][3][N]
+  cplx<T>* n;            // [N]      n = (1/Nk) sum_q f conj(bra_q) ket_q
+  cplx<T>* m;            // [3][N]   (1/Nk) sum_q f conj(bra_q) grad ket_q
+  cplx<T>* nt;           // [N]      FT[n] (1/N normalised)
+  cplx<T>* mt;           // [3][N]   FT[m]
+  cplx<T>* vH;           // [N]
+  cplx<T>* h1;           // [3][N]
+  cplx<T>* vb2;          // [N]
+  cplx<T>* t3b1;         // [N]
+  cplx<T>* t3b2;         // [N]
+  cplx<T>* vu;           // [2][N]   sum_{G != 0} u~_s(G) n~(G) e^{iG.r}  (no 1/Omega)
+  cplx<T>* spec;         // [3][N]   spectral scratch
+  cplx<T>* h3a4;         // [Nk][no][3][N]
+  cplx<T>* h3b;          // [Nk][no][3][N]
+  cplx<T>* h5;           // [3][N]
+  cplx<T>* h6;           // [N]
+  cplx<T>* vloc;         // [N]
+  cplx<T>* acc;          // [Nk][nb][N]  output accumulator (real space)
+  cplx<T>* w;            // [Nk][nb][3][N]
+  double* cs;            // [Nk*nb][no][6]: O_qj, X_pp, X_ap (re, im each): 3b6 correction scalars
+  const T* tabV;         // [ndelta][2][N] -> this side's V at offset side*N
+  T s2b;                 // +1 right, -1 left (sign of the grad u . grad terms)
+  int side;
+};
+
+template <typename T> struct Params {
+  int Nk, nb, no, npw_max, ndelta;
+  int nsmem;             // number of n^3 volumes held in shared memory
+  int div;
+  T Bm[3][3];            // reciprocal rows b_i
+  T invN;
+  double Omega, invOm2;
+  double corr_c[2], A[2];
+  T tw[NT];              // per-term weights (1 apply, 1/2 or 1/3 energy, 0 = off)
+  const int* delta_id;   // [Nk][Nk]
+  const T* delta;        // [ndelta][3]
+  const T* tabU;         // [ndelta][2][N] u~_pp/Omega, u~_ap/Omega
+  const T* tabV;         // [ndelta][2][N]
+  const T* hartV;        // [2][N]
+  const T* hartU;        // [N]
+  const T* hartUs;       // [2][N] (no 1/Omega)
+  const double* occ;     // [Nk][nb]
+  cplx<T>* scratch;      // per-CTA volumes
+  SideArgs<T> side[2];
+};
+
+}  // namespace tc

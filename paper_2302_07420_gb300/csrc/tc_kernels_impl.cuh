@@ -1,0 +1,666 @@
+// Kernels of the TC operator (templated on precision T and cubic box size N).
+//
+// Stage map (Sec. 2.7 of arXiv:2302.07420):
+//   k_orbitals     sphere -> box gather and inverse FFT of phi, chi, grad phi, grad chi
+//   k_density      n and the 2bh2 vector density m (per side)
+//   k_spec_fwd     FT of a global field or of a product of two fields
+//   k_hartree_inv  Hartree-type convolutions: v_H (Alg. 1), h1 (Algs. 3, 5, 7, 9),
+//                  v_b2 (2bh2), the 3b1 / 3b2 tails and the 3b6 scf2 field
+//   k_occ_pairs    occupied-pair stage (Algs. 4, 6, 8, 11): h6, h3 (3a4), h3 (3b), and
+//                  the 3a2 corrections (Eqs. divcor_3a2_first/second, general overlaps)
+//   k_reduce_a4    sum of the per-CTA h6 parts and h5 of Alg. 8
+//   k_vloc         local potential of the Hartree-type terms
+//   k_pair_chain   per output orbital j, all partners q: 2ax (Alg. 2), 2bx1, 2bx2, 3a3's w_j,
+//                  3a4 (Alg. 6), 3b3 (Alg. 9), 3b5 (Alg. 11), 3b6 (Alg. 12) fused into one
+//                  FFT chain per (j, q) pair
+//   k_pair_3b4     second pass for 3b4 (Alg. 10), which needs the complete w_j
+//   k_finalize     local terms, 3b6 corrections (Eqs. 3b6_div_scf1/2/3), FFT, box -> sphere
+#pragma once
+#include "tc_kernels.cuh"
+
+namespace tc {
+
+template <int N> struct Cfg {
+  static constexpr int threads = (N * N <= 384) ? ((N * N + 31) / 32) * 32 : ((N * N / 2 + 31) / 32) * 32;
+};
+
+template <typename T, int N> __device__ __forceinline__ cplx<T>* vol_slot(const Params<T>& P, cplx<T>* smem, int slot,
+                                                                           int nslots, bool force_global = false) {
+  if (!force_global && slot < P.nsmem) return smem + (size_t)slot * Geo<N>::vol;
+  const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  return P.scratch + (cta * nslots + slot) * (size_t)Geo<N>::vol;
+}
+
+// p = Delta + G for the FFT index (i1, i2, i3)
+template <typename T, int N> __device__ __forceinline__ void pvec(const Params<T>& P, const T* dl, int i1, int i2, int i3,
+                                                                   T* p) {
+  const T r1 = (T)(i1 <= (N - 1) / 2 ? i1 : i1 - N);
+  const T r2 = (T)(i2 <= (N - 1) / 2 ? i2 : i2 - N);
+  const T r3 = (T)(i3 <= (N - 1) / 2 ? i3 : i3 - N);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p[d] = dl[d] + r1 * P.Bm[0][d] + r2 * P.Bm[1][d] + r3 * P.Bm[2][d];
+}
+
+template <typename T> __device__ __forceinline__ cplx<T> ld(const cplx<T>* p, size_t i) { return p[i]; }
+
+template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += red[i];
+  return s;   // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// Standalone batched 3D FFT (testing hook).
+template <typename T, int N, int S> __global__ void __launch_bounds__(Cfg<N>::threads) k_fft3d(cplx<T>* data) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* d = data + (size_t)blockIdx.x * G::nn;
+  auto ld = [&](int a, int b, int c) { return d[G::gidx(a, b, c)]; };
+  auto st = [&](int a, int b, int c, cplx<T> v) { d[G::gidx(a, b, c)] = v; };
+  if (S < 0) fwd3d<T, N>(V, ld, st);
+  else inv3d<T, N>(V, ld, st);
+}
+
+// ---------------------------------------------------------------------------
+// Orbitals to real space: grid (Nk*nb, 4 components, 2 sets).  Component 0 is
+// psi = FT^{-1}[c], components 1..3 are d_d psi = FT^{-1}[i (k+G)_d c].
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads)
+    k_orbitals(const double2* __restrict__ cphi, const double2* __restrict__ cchi, const int* __restrict__ box_index,
+               const double* __restrict__ kpg, int npw_max, int nb, cplx<T>* phi, cplx<T>* chi, cplx<T>* gphi,
+               cplx<T>* gchi) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  const int j = blockIdx.x, comp = blockIdx.y, set = blockIdx.z;
+  const int k = j / nb;
+  const double2* c = (set == 0 ? cphi : cchi) + (size_t)j * npw_max;
+  for (int i = threadIdx.x; i < G::vol; i += blockDim.x) V[i] = cplx<T>{0, 0};
+  __syncthreads();
+  for (int g = threadIdx.x; g < npw_max; g += blockDim.x) {
+    const int bi = box_index[(size_t)k * npw_max + g];
+    if (bi < 0) continue;
+    double2 v = c[g];
+    if (comp > 0) {   // multiply by i (k+G)_d
+      const double q = kpg[((size_t)k * npw_max + g) * 3 + (comp - 1)];
+      v = make_double2(-q * v.y, q * v.x);
+    }
+    const int i1 = bi / (N * N), i2 = (bi / N) % N, i3 = bi % N;
+    V[G::sidx(i1, i2, i3)] = cplx<T>{(T)v.x, (T)v.y};
+  }
+  __syncthreads();
+  cplx<T>* dst = comp == 0 ? (set == 0 ? phi : chi) + (size_t)j * G::nn
+                           : (set == 0 ? gphi : gchi) + ((size_t)j * 3 + (comp - 1)) * G::nn;
+  inv3d<T, N>(V, [&](int a, int b, int cc) { return V[G::sidx(a, b, cc)]; },
+              [&](int a, int b, int cc, cplx<T> v) { dst[G::gidx(a, b, cc)] = v; });
+}
+
+// ---------------------------------------------------------------------------
+// Densities of both sides: n = (1/Nk) sum_{k, mu < no} f conj(bra) ket, m likewise with grad ket.
+template <typename T, int N> __global__ void k_density(Params<T> P) {
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int NN = N * N * N;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < NN; r += gridDim.x * blockDim.x) {
+    cplx<T> n = {0, 0}, m0 = {0, 0}, m1 = {0, 0}, m2 = {0, 0};
+    for (int k = 0; k < P.Nk; ++k)
+      for (int mu = 0; mu < P.no; ++mu) {
+        const int q = k * P.nb + mu;
+        const T f = (T)(P.occ[q] / P.Nk);
+        if (f == T(0)) continue;
+        const cplx<T> b = conjg(S.bra[(size_t)q * NN + r]);
+        n = n + f * (b * S.ket[(size_t)q * NN + r]);
+        m0 = m0 + f * (b * S.gket[((size_t)q * 3 + 0) * NN + r]);
+        m1 = m1 + f * (b * S.gket[((size_t)q * 3 + 1) * NN + r]);
+        m2 = m2 + f * (b * S.gket[((size_t)q * 3 + 2) * NN + r]);
+      }
+    S.n[r] = n;
+    S.m[r] = m0;
+    S.m[NN + r] = m1;
+    S.m[2 * NN + r] = m2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dst[c] = FT[a[c] * b[c]] (1/N normalised) for c = blockIdx.x; b may be null (factor 1).
+// blockIdx.y = side; a and b are given per side by offsets into the side's fields.
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads)
+    k_spec_fwd(Params<T> P, int which) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int c = blockIdx.x;
+  const cplx<T>* a;
+  const cplx<T>* b = nullptr;
+  cplx<T>* dst;
+  if (which == 0) {          // n~
+    a = S.n; dst = S.nt;
+  } else if (which == 1) {   // m~_c
+    a = S.m + (size_t)c * G::nn; dst = S.mt + (size_t)c * G::nn;
+  } else if (which == 2) {   // FT[h1_c n]  (Alg. 7 line 4)
+    a = S.h1 + (size_t)c * G::nn; b = S.n; dst = S.spec + (size_t)c * G::nn;
+  } else {                   // FT[h5_c]    (Alg. 8 line 16)
+    a = S.h5 + (size_t)c * G::nn; dst = S.spec + (size_t)c * G::nn;
+  }
+  fwd3d<T, N>(
+      V,
+      [&](int i, int j, int k) {
+        cplx<T> v = a[G::gidx(i, j, k)];
+        return b ? v * b[G::gidx(i, j, k)] : v;
+      },
+      [&](int i, int j, int k, cplx<T> v) { dst[G::gidx(i, j, k)] = P.invN * v; });
+}
+
+// Hartree-type convolutions (Delta = 0, G = 0 dropped), blockIdx.y = side.
+//   kind 0: v_H = FT^{-1}[Vh n~]
+//   kind 1: h1_c = FT^{-1}[i G_c u~h n~]                 (c = blockIdx.x)
+//   kind 2: v_b2 = FT^{-1}[-i G u~h . m~]
+//   kind 3: t3b1 = FT^{-1}[-i G u~h . FT[h1 n]]         (spectrum in S.spec)
+//   kind 4: t3b2 = FT^{-1}[-i G u~h . FT[h5]]           (spectrum in S.spec)
+//   kind 5: vu_s = FT^{-1}[u~_s n~] (no 1/Omega)        (s = blockIdx.x)
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads)
+    k_hartree_inv(Params<T> P, int kind) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int c = blockIdx.x;
+  const T zero3[3] = {0, 0, 0};
+  cplx<T>* dst = kind == 0 ? S.vH : kind == 1 ? S.h1 + (size_t)c * G::nn : kind == 2 ? S.vb2 : kind == 3 ? S.t3b1
+               : kind == 4 ? S.t3b2 : S.vu + (size_t)c * G::nn;
+  inv3d<T, N>(
+      V,
+      [&](int i, int j, int k) {
+        const int g = G::gidx(i, j, k);
+        if (kind == 0) return P.hartV[(size_t)S.side * G::nn + g] * S.nt[g];
+        if (kind == 5) return P.hartUs[(size_t)c * G::nn + g] * S.nt[g];
+        T p[3];
+        pvec<T, N>(P, zero3, i, j, k, p);
+        const T u = P.hartU[g];
+        if (kind == 1) {
+          const cplx<T> t = (p[c] * u) * S.nt[g];
+          return mul_si<T, 1>(t);
+        }
+        const cplx<T>* src = (kind == 2) ? S.mt : S.spec;
+        cplx<T> s = {0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s = s + (p[d] * u) * src[(size_t)d * G::nn + g];
+        return mul_si<T, -1>(s);   // -i G u . src
+      },
+      [&](int i, int j, int k, cplx<T> v) { dst[G::gidx(i, j, k)] = v; });
+}
+
+// ---------------------------------------------------------------------------
+// Occupied-pair stage.  Grid (Nk*no, 2 sides); CTA = occupied q2, loop over q1.
+//   P^s(a, b) = FT^{-1}[U^_s(k_b - k_a + G) FT[conj(bra_a) ket_b]],  U^_s = i p u~_s / Omega
+//   h6 += f1 f2 / Nk^2 sum_s P^s(q2,q1) . P^s(q1,q2)             (Alg. 4)
+//   h3a4(q2) += f1/Nk P^pp(q1,q2) ket_q1                         (Alg. 6)
+//   h3b(q2)  += f1/Nk P^pp(q2,q1) conj(bra_q1)                   (Algs. 8, 11)
+// Slots: 0 B1, 1 B2, 2 A1, 3 A2 (shared or global), 4 h6 part, 5 F_ab (global).
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
+  using G = Geo<N>;
+  constexpr int NS = 6;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+  __shared__ double sO[2][2];
+  __shared__ double sF0[2];
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int k2 = blockIdx.x / P.no, mu2 = blockIdx.x % P.no;
+  const int q2 = k2 * P.nb + mu2;
+  cplx<T>* B1 = vol_slot<T, N>(P, sm, 0, NS);
+  cplx<T>* B2 = vol_slot<T, N>(P, sm, 1, NS);
+  cplx<T>* A1 = vol_slot<T, N>(P, sm, 2, NS);
+  cplx<T>* A2 = vol_slot<T, N>(P, sm, 3, NS);
+  cplx<T>* H6 = vol_slot<T, N>(P, sm, 4, NS, true);
+  cplx<T>* FAB = vol_slot<T, N>(P, sm, 5, NS, true);
+  const size_t NN = G::nn;
+  const T f2 = (T)(P.occ[q2] / P.Nk);
+  cplx<T>* h3a4 = S.h3a4 + ((size_t)(k2 * P.no + mu2) * 3) * NN;
+  cplx<T>* h3b = S.h3b + ((size_t)(k2 * P.no + mu2) * 3) * NN;
+  const cplx<T>* bra2 = S.bra + (size_t)q2 * NN;
+  const cplx<T>* ket2 = S.ket + (size_t)q2 * NN;
+  for (int r = threadIdx.x; r < G::vol; r += blockDim.x) FAB[r] = cplx<T>{0, 0};   // padded layout
+  for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
+    H6[r] = cplx<T>{0, 0};
+    for (int d = 0; d < 3; ++d) {
+      h3a4[d * NN + r] = cplx<T>{0, 0};
+      h3b[d * NN + r] = cplx<T>{0, 0};
+    }
+  }
+  if (threadIdx.x == 0) { sF0[0] = 0.0; sF0[1] = 0.0; }
+  __syncthreads();
+  for (int k1 = 0; k1 < P.Nk; ++k1) {
+    const int id12 = P.delta_id[k2 * P.Nk + k1];   // Delta = k2 - k1 -> for P(q1,q2)
+    const int id21 = P.delta_id[k1 * P.Nk + k2];   // Delta = k1 - k2 -> for P(q2,q1)
+    const T* d12 = P.delta + id12 * 3;
+    const T* d21 = P.delta + id21 * 3;
+    for (int mu1 = 0; mu1 < P.no; ++mu1) {
+      const int q1 = k1 * P.nb + mu1;
+      const T f1 = (T)(P.occ[q1] / P.Nk);
+      if (f1 == T(0) || f2 == T(0)) continue;
+      const cplx<T>* bra1 = S.bra + (size_t)q1 * NN;
+      const cplx<T>* ket1 = S.ket + (size_t)q1 * NN;
+      // A1 = FT[conj(bra_q2) ket_q1], A2 = FT[conj(bra_q1) ket_q2]
+      fwd3d<T, N>(B1, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ket1[g], bra2[g]); },
+                  [&](int i, int j, int k, cplx<T> v) { A1[G::sidx(i, j, k)] = P.invN * v; });
+      fwd3d<T, N>(B2, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ket2[g], bra1[g]); },
+                  [&](int i, int j, int k, cplx<T> v) { A2[G::sidx(i, j, k)] = P.invN * v; });
+      __syncthreads();
+      // 3a2 correction pieces for pairs at the same k (Eqs. divcor_3a2_*_density_matrix_mixing)
+      if (P.div && k1 == k2) {
+        if (threadIdx.x == 0) {
+          const cplx<T> o21 = A1[0], o12 = A2[0];   // <bra_q2|ket_q1>, <bra_q1|ket_q2>
+          sO[0][0] = o21.x; sO[0][1] = o21.y; sO[1][0] = o12.x; sO[1][1] = o12.y;
+          const double fq = P.occ[q1];
+          sF0[0] += fq * ((double)o21.x * o12.x - (double)o21.y * o12.y);
+          sF0[1] += fq * ((double)o21.x * o12.y + (double)o21.y * o12.x);
+        }
+        __syncthreads();
+        const cplx<T> o21 = {(T)sO[0][0], (T)sO[0][1]}, o12 = {(T)sO[1][0], (T)sO[1][1]};
+        const T fq = (T)P.occ[q1];
+        for (int r = threadIdx.x; r < G::vol; r += blockDim.x) FAB[r] = FAB[r] + fq * (o12 * A1[r] + o21 * A2[r]);
+        __syncthreads();
+      }
+      for (int sp = 0; sp < 2; ++sp) {
+        for (int d = 0; d < 3; ++d) {
+          // B1 = P^s_d(q2, q1) (stored), B2 = P^s_d(q1, q2) (consumed with B1 in the last pass)
+          inv3d<T, N>(
+              B1,
+              [&](int i, int j, int k) {
+                T p[3];
+                pvec<T, N>(P, d21, i, j, k, p);
+                const T u = P.tabU[((size_t)id21 * 2 + sp) * NN + G::gidx(i, j, k)];
+                return mul_si<T, 1>((p[d] * u) * A1[G::sidx(i, j, k)]);
+              },
+              [&](int i, int j, int k, cplx<T> v) { B1[G::sidx(i, j, k)] = v; });
+          inv3d<T, N>(
+              B2,
+              [&](int i, int j, int k) {
+                T p[3];
+                pvec<T, N>(P, d12, i, j, k, p);
+                const T u = P.tabU[((size_t)id12 * 2 + sp) * NN + G::gidx(i, j, k)];
+                return mul_si<T, 1>((p[d] * u) * A2[G::sidx(i, j, k)]);
+              },
+              [&](int i, int j, int k, cplx<T> b2) {
+                // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
+                const int g = G::gidx(i, j, k);
+                const cplx<T> b1 = B1[G::sidx(i, j, k)];
+                H6[g] = H6[g] + (f1 * f2) * (b1 * b2);
+                if (sp == 0) {
+                  h3a4[d * NN + g] = h3a4[d * NN + g] + f1 * (b2 * ket1[g]);
+                  h3b[d * NN + g] = h3b[d * NN + g] + f1 * mulc(b1, bra1[g]);
+                }
+              });
+          __syncthreads();
+        }
+      }
+    }
+  }
+  // 3a2 corrections of this q2: (f2/Nk)/Omega^2 sum_s [c_s F0 + (4 pi A_s/Nk) FT^{-1}[u~_s F_ab]]
+  if (P.div && f2 != T(0)) {
+    const T pref = (T)(f2 * P.invOm2);
+    const T c0 = (T)(P.corr_c[0] + P.corr_c[1]);
+    const cplx<T> cF0 = {(T)(c0 * sF0[0]), (T)(c0 * sF0[1])};
+    const T a0 = (T)(4.0 * 3.14159265358979323846 * P.A[0] / P.Nk), a1 = (T)(4.0 * 3.14159265358979323846 * P.A[1] / P.Nk);
+    inv3d<T, N>(
+        B1,
+        [&](int i, int j, int k) {
+          const int g = G::gidx(i, j, k);
+          const T u = a0 * P.hartUs[g] + a1 * P.hartUs[NN + g];
+          return u * FAB[G::sidx(i, j, k)];
+        },
+        [&](int i, int j, int k, cplx<T> v) {
+          const int g = G::gidx(i, j, k);
+          H6[g] = H6[g] + pref * (v + cF0);
+        });
+  }
+}
+
+// h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8 lines 9-10)
+template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
+  using G = Geo<N>;
+  constexpr int NS = 6;
+  const int side = blockIdx.y;
+  const SideArgs<T>& S = P.side[side];
+  const size_t NN = G::nn;
+  const int ncta = P.Nk * P.no;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < (int)NN; r += gridDim.x * blockDim.x) {
+    cplx<T> h6 = {0, 0}, h5[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int c = 0; c < ncta; ++c) {
+      const size_t cta = (size_t)side * ncta + c;
+      h6 = h6 + P.scratch[(cta * NS + 4) * (size_t)Geo<N>::vol + r];
+      const int k = c / P.no, mu = c % P.no;
+      const int q = k * P.nb + mu;
+      const T f = (T)(P.occ[q] / P.Nk);
+      const cplx<T> kv = S.ket[(size_t)q * NN + r];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) h5[d] = h5[d] + f * (S.h3b[((size_t)c * 3 + d) * NN + r] * kv);
+    }
+    S.h6[r] = h6;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S.h5[d * NN + r] = h5[d];
+  }
+}
+
+// Local potential: tw2ah v_H + tw2bh2 s2b v_b2 - tw3a1 h1.h1/2 + tw3a2 h6/2 - tw3b1 t3b1 + tw3b2 t3b2
+template <typename T, int N> __global__ void k_vloc(Params<T> P) {
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const size_t NN = (size_t)N * N * N;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < (int)NN; r += gridDim.x * blockDim.x) {
+    cplx<T> h1h1 = {0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) h1h1 = h1h1 + S.h1[d * NN + r] * S.h1[d * NN + r];
+    cplx<T> v = P.tw[T2AH] * S.vH[r] + (P.tw[T2BH2] * S.s2b) * S.vb2[r] - (T(0.5) * P.tw[T3A1]) * h1h1 +
+                (T(0.5) * P.tw[T3A2]) * S.h6[r] - P.tw[T3B1] * S.t3b1[r] + P.tw[T3B2] * S.t3b2[r];
+    S.vloc[r] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused pair chains, pass 1.  Grid (Nk*nb, 2 sides); CTA = output orbital j.
+// For every occupied partner q (f = f_q / Nk, rho = conj(bra_q) ket_j):
+//   A  = FT[rho]
+//   2ax : acc -= tw f ket_q FT^{-1}[V(Delta + G) A]
+//   for d: b = FT^{-1}[U^pp_d A]
+//        acc -= s2b tw2bx1 f d_d ket_q b + tw3a4 f h3a4(q)_d b;   w_d += f ket_q b
+//        F   = tw3b3 h1_d rho - tw3b5 ket_j h3b(q)_d + tw3b6 n b - s2b tw2bx2 conj(bra_q) d_d ket_j
+//        C  += -U^pp_d FT[F]
+//   for d: b = FT^{-1}[U^ap_d A];  C += -U^ap_d FT[tw3b6 n b]
+//   acc += f ket_q FT^{-1}[C]
+// The inverse transform of b ends on axis 1 and the forward transform of F
+// starts on axis 1, so one thread owns each pencil through the pointwise work.
+// When k_q = k_j the CTA also stores O_qj = A(0) and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G)
+// for the 3b6 corrections.  Slots: 0 B, 1 A, 2 C.
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) {
+  using G = Geo<N>;
+  constexpr int NS = 3;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+  __shared__ T red[32];
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int j = blockIdx.x, kj = j / P.nb;
+  cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
+  cplx<T>* A = vol_slot<T, N>(P, sm, 1, NS);
+  cplx<T>* C = vol_slot<T, N>(P, sm, 2, NS);
+  const size_t NN = G::nn;
+  const cplx<T>* ketj = S.ket + (size_t)j * NN;
+  const cplx<T>* gketj = S.gket + (size_t)j * 3 * NN;
+  cplx<T>* acc = S.acc + (size_t)j * NN;
+  cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  const T* tw = P.tw;
+  const T s2b = S.s2b;
+  const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
+  const bool need_pp = need_w || tw[T2BX1] != T(0) || tw[T3A4] != T(0) || tw[T3B6] != T(0);
+  const bool need_F = tw[T3B3] != T(0) || tw[T3B5] != T(0) || tw[T3B6] != T(0) || tw[T2BX2] != T(0);
+  const bool need_ap = tw[T3B6] != T(0);
+  for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
+    acc[r] = cplx<T>{0, 0};
+    for (int d = 0; d < 3; ++d) w[d * NN + r] = cplx<T>{0, 0};
+  }
+  __syncthreads();
+  for (int kq = 0; kq < P.Nk; ++kq) {
+    const int did = P.delta_id[kj * P.Nk + kq];
+    const T* dl = P.delta + did * 3;
+    const T* Vt = S.tabV + ((size_t)did * 2 + S.side) * NN;
+    const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
+    const T* Uap = P.tabU + ((size_t)did * 2 + 1) * NN;
+    for (int mu = 0; mu < P.no; ++mu) {
+      const int q = kq * P.nb + mu;
+      const T f = (T)(P.occ[q] / P.Nk);
+      if (f == T(0)) continue;
+      const cplx<T>* braq = S.bra + (size_t)q * NN;
+      const cplx<T>* ketq = S.ket + (size_t)q * NN;
+      const cplx<T>* gketq = S.gket + (size_t)q * 3 * NN;
+      const cplx<T>* h3a4q = S.h3a4 + ((size_t)(kq * P.no + mu) * 3) * NN;
+      const cplx<T>* h3bq = S.h3b + ((size_t)(kq * P.no + mu) * 3) * NN;
+      // A = FT[conj(bra_q) ket_j]
+      fwd3d<T, N>(B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ketj[g], braq[g]); },
+                  [&](int a, int b, int c, cplx<T> v) { A[G::sidx(a, b, c)] = P.invN * v; });
+      __syncthreads();
+      if (P.div && kq == kj && tw[T3B6] != T(0)) {
+        // O_qj and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G)
+        for (int s = 0; s < 2; ++s) {
+          T xr = 0, xi = 0;
+          for (int g = threadIdx.x; g < (int)NN; g += blockDim.x) {
+            const int a = g / (N * N), b = (g / N) % N, c = g % N;
+            const int gn = G::gidx((N - a) % N, (N - b) % N, (N - c) % N);
+            const cplx<T> t = P.hartUs[(size_t)s * NN + g] * (A[G::sidx(a, b, c)] * S.nt[gn]);
+            xr += t.x;
+            xi += t.y;
+          }
+          const T sr = block_sum<T>(xr, red);
+          const T si = block_sum<T>(xi, red);
+          if (threadIdx.x == 0) {
+            double* cs = S.cs + ((size_t)j * P.no + mu) * 6;
+            cs[2 + 2 * s] = sr;
+            cs[3 + 2 * s] = si;
+            if (s == 0) { cs[0] = A[0].x; cs[1] = A[0].y; }
+          }
+        }
+        __syncthreads();
+      }
+      // 2ax
+      if (tw[T2AX] != T(0)) {
+        const T fw = -f * tw[T2AX];
+        inv3d<T, N>(B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
+                    [&](int a, int b, int c, cplx<T> v) {
+                      const int g = G::gidx(a, b, c);
+                      acc[g] = acc[g] + fw * (ketq[g] * v);
+                    });
+        __syncthreads();
+      }
+      // grad-u channels: pp (with the fused second-stage vector field) and ap (3b6)
+      for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 0 && !(need_pp || need_F)) continue;
+        if (sp == 1 && !need_ap) continue;
+        const T* Ut = sp == 0 ? Upp : Uap;
+        for (int d = 0; d < 3; ++d) {
+          const bool first_C = (sp == 0 && d == 0);
+          // b = FT^{-1}[U_d A]: axes 2 and 3 here, axis 1 fused below
+          fft_pass<T, N, +1, 2>(
+              [&](int a, int b, int c) {
+                T p[3];
+                pvec<T, N>(P, dl, a, b, c, p);
+                return mul_si<T, 1>((p[d] * Ut[G::gidx(a, b, c)]) * A[G::sidx(a, b, c)]);
+              },
+              [&](int a, int b, int c, cplx<T> v) { B[G::sidx(a, b, c)] = v; });
+          __syncthreads();
+          fft_pass<T, N, +1, 3>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
+                                [&](int a, int b, int c, cplx<T> v) { B[G::sidx(a, b, c)] = v; });
+          __syncthreads();
+          // axis 1: inverse, pointwise work, forward (one thread owns each (i2, i3) pencil)
+          for (int pp = threadIdx.x; pp < N * N; pp += blockDim.x) {
+            const int i2 = pp / N, i3 = pp % N;
+            cplx<T> v[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[i] = B[G::sidx(i, i2, i3)];
+            Codelet<T, N, +1>::run(v);
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              const int g = G::gidx(i, i2, i3);
+              const cplx<T> bv = v[i];
+              cplx<T> F = {0, 0};
+              if (sp == 0) {
+                const cplx<T> kqv = ketq[g];
+                cplx<T> da = {0, 0};
+                if (tw[T2BX1] != T(0)) da = da + (-s2b * tw[T2BX1] * f) * (gketq[d * NN + g] * bv);
+                if (tw[T3A4] != T(0)) da = da + (-tw[T3A4] * f) * (h3a4q[d * NN + g] * bv);
+                if (tw[T2BX1] != T(0) || tw[T3A4] != T(0)) acc[g] = acc[g] + da;
+                if (need_w) w[d * NN + g] = w[d * NN + g] + f * (kqv * bv);
+                if (need_F) {
+                  const cplx<T> kj_ = ketj[g];
+                  if (tw[T3B3] != T(0)) F = F + tw[T3B3] * (S.h1[d * NN + g] * mulc(kj_, braq[g]));
+                  if (tw[T3B5] != T(0)) F = F - tw[T3B5] * (kj_ * h3bq[d * NN + g]);
+                  if (tw[T3B6] != T(0)) F = F + tw[T3B6] * (S.n[g] * bv);
+                  if (tw[T2BX2] != T(0)) F = F - (s2b * tw[T2BX2]) * mulc(gketj[d * NN + g], braq[g]);
+                }
+              } else {
+                F = tw[T3B6] * (S.n[g] * bv);
+              }
+              v[i] = F;
+            }
+            if (sp == 0 && !need_F) continue;
+            Codelet<T, N, -1>::run(v);
+#pragma unroll
+            for (int i = 0; i < N; ++i) B[G::sidx(i, i2, i3)] = v[i];
+          }
+          __syncthreads();
+          if (sp == 0 && !need_F) continue;
+          fft_pass<T, N, -1, 3>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
+                                [&](int a, int b, int c, cplx<T> v) { B[G::sidx(a, b, c)] = v; });
+          __syncthreads();
+          fft_pass<T, N, -1, 2>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
+                                [&](int a, int b, int c, cplx<T> v) {
+                                  T p[3];
+                                  pvec<T, N>(P, dl, a, b, c, p);
+                                  // -U_d FT[F] = -i p_d u (v / N)
+                                  const cplx<T> t = mul_si<T, -1>((p[d] * Ut[G::gidx(a, b, c)] * P.invN) * v);
+                                  const int s = G::sidx(a, b, c);
+                                  C[s] = first_C ? t : C[s] + t;
+                                });
+          __syncthreads();
+        }
+      }
+      if (need_F || need_ap) {
+        inv3d<T, N>(B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
+                    [&](int a, int b, int c, cplx<T> v) {
+                      const int g = G::gidx(a, b, c);
+                      acc[g] = acc[g] + f * (ketq[g] * v);
+                    });
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// Pass 2 for 3b4 (Alg. 10): acc += tw f ket_q FT^{-1}[-U^pp . FT[-conj(bra_q) w_j]].
+// Slots: 0 B (work), 1 A (spectral accumulator).
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
+  using G = Geo<N>;
+  constexpr int NS = 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const int j = blockIdx.x, kj = j / P.nb;
+  cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
+  cplx<T>* A = vol_slot<T, N>(P, sm, 1, NS);
+  const size_t NN = G::nn;
+  cplx<T>* acc = S.acc + (size_t)j * NN;
+  const cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  const T t3b4 = P.tw[T3B4];
+  if (t3b4 == T(0)) return;
+  for (int kq = 0; kq < P.Nk; ++kq) {
+    const int did = P.delta_id[kj * P.Nk + kq];
+    const T* dl = P.delta + did * 3;
+    const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
+    for (int mu = 0; mu < P.no; ++mu) {
+      const int q = kq * P.nb + mu;
+      const T f = (T)(P.occ[q] / P.Nk);
+      if (f == T(0)) continue;
+      const cplx<T>* braq = S.bra + (size_t)q * NN;
+      const cplx<T>* ketq = S.ket + (size_t)q * NN;
+      for (int d = 0; d < 3; ++d) {
+        fwd3d<T, N>(
+            B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(w[d * NN + g], braq[g]); },
+            [&](int a, int b, int c, cplx<T> v) {
+              T p[3];
+              pvec<T, N>(P, dl, a, b, c, p);
+              // -U_d FT[-conj(bra_q) w_d] = +i p_d u FT[conj(bra_q) w_d]
+              const cplx<T> t = mul_si<T, 1>((p[d] * Upp[G::gidx(a, b, c)] * P.invN) * v);
+              const int s = G::sidx(a, b, c);
+              A[s] = d == 0 ? t : A[s] + t;
+            });
+        __syncthreads();
+      }
+      const T fw = t3b4 * f;
+      inv3d<T, N>(B, [&](int a, int b, int c) { return A[G::sidx(a, b, c)]; },
+                  [&](int a, int b, int c, cplx<T> v) {
+                    const int g = G::gidx(a, b, c);
+                    acc[g] = acc[g] + fw * (ketq[g] * v);
+                  });
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalize: acc += vloc ket_j + s2b tw2bh1 h1 . grad ket_j + tw3a3 h1 . w_j + 3b6 corrections,
+// then out(G) = FT[acc](G) on the sphere of k_j (FP64 interleaved complex).
+template <typename T, int N>
+__global__ void __launch_bounds__(Cfg<N>::threads)
+    k_finalize(Params<T> P, double2* outR, double2* outL, const int* __restrict__ box_index) {
+  using G = Geo<N>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  const int side = blockIdx.y;
+  const SideArgs<T>& S = P.side[side];
+  double2* out = side == 0 ? outR : outL;
+  if (out == nullptr) return;
+  const int j = blockIdx.x, kj = j / P.nb;
+  const size_t NN = G::nn;
+  const cplx<T>* ketj = S.ket + (size_t)j * NN;
+  const cplx<T>* gketj = S.gket + (size_t)j * 3 * NN;
+  const cplx<T>* acc = S.acc + (size_t)j * NN;
+  const cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  const T t2bh1 = P.tw[T2BH1] * S.s2b, t3a3 = P.tw[T3A3];
+  const bool corr = P.div && P.tw[T3B6] != T(0);
+  const T a0 = (T)(4.0 * 3.14159265358979323846 * P.A[0] / P.Nk), a1 = (T)(4.0 * 3.14159265358979323846 * P.A[1] / P.Nk);
+  const double n0x = corr ? (double)S.nt[0].x : 0.0, n0y = corr ? (double)S.nt[0].y : 0.0;
+  fwd3d<T, N>(
+      V,
+      [&](int a, int b, int c) {
+        const int g = G::gidx(a, b, c);
+        const cplx<T> kv = ketj[g];
+        cplx<T> v = acc[g] + S.vloc[g] * kv;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const cplx<T> h = S.h1[d * NN + g];
+          v = v + t2bh1 * (h * gketj[d * NN + g]) + t3a3 * (h * w[d * NN + g]);
+        }
+        if (corr) {
+          // sum_q f_q ket_q (1/Omega^2) sum_s [c_s n0 O_qj + (4 pi A_s/Nk)(O_qj vu_s + X_s)]
+          cplx<T> s = {0, 0};
+          for (int mu = 0; mu < P.no; ++mu) {
+            const int q = kj * P.nb + mu;
+            const double fq = P.occ[q];
+            if (fq == 0.0) continue;
+            const double* cs = S.cs + ((size_t)j * P.no + mu) * 6;
+            const cplx<T> O = {(T)cs[0], (T)cs[1]};
+            const cplx<T> X0 = {(T)cs[2], (T)cs[3]}, X1 = {(T)cs[4], (T)cs[5]};
+            const double cc = P.corr_c[0] + P.corr_c[1];
+            const cplx<T> cn = {(T)(cc * n0x), (T)(cc * n0y)};
+            cplx<T> t = cn * O + a0 * (O * S.vu[g] + X0) + a1 * (O * S.vu[NN + g] + X1);
+            s = s + (T)(fq * P.invOm2) * (S.ket[(size_t)q * NN + g] * t);
+          }
+          v = v + P.tw[T3B6] * s;
+        }
+        return v;
+      },
+      [&](int a, int b, int c, cplx<T> v) { V[G::sidx(a, b, c)] = P.invN * v; });
+  __syncthreads();
+  double2* o = out + (size_t)j * P.npw_max;
+  for (int g = threadIdx.x; g < P.npw_max; g += blockDim.x) {
+    const int bi = box_index[(size_t)kj * P.npw_max + g];
+    if (bi < 0) {
+      o[g] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const int i1 = bi / (N * N), i2 = (bi / N) % N, i3 = bi % N;
+    const cplx<T> v = V[G::sidx(i1, i2, i3)];
+    o[g] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+}  // namespace tc

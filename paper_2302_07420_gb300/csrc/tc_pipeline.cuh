@@ -1,0 +1,241 @@
+// Host-side launch sequence of the operator for one (precision, box size).
+#pragma once
+#include <cmath>
+#include <cstdio>
+
+#include "tc_ctx.hpp"
+#include "tc_kernels_impl.cuh"
+
+namespace tc {
+
+constexpr int kSmemLimit = 227 * 1024;   // bytes of shared memory per CTA on sm_103a
+
+template <typename T> static inline size_t side_field_vols(int Nk, int nb, int no) {
+  // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc  = 25
+  return 25 + (size_t)Nk * no * 3 * 2 + (size_t)Nk * nb * (1 + 3);
+}
+
+template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideArgs<T>& s) {
+  const size_t NN = (size_t)N * N * N;
+  const auto& S = ctx->S;
+  cplx<T>* base = reinterpret_cast<cplx<T>*>(reinterpret_cast<char*>(ctx->d_side) + side * ctx->side_bytes);
+  size_t o = 0;
+  auto take = [&](size_t vols) { cplx<T>* p = base + o * NN; o += vols; return p; };
+  s.n = take(1); s.m = take(3); s.nt = take(1); s.mt = take(3); s.vH = take(1); s.h1 = take(3);
+  s.vb2 = take(1); s.t3b1 = take(1); s.t3b2 = take(1); s.vu = take(2); s.spec = take(3); s.h5 = take(3);
+  s.h6 = take(1); s.vloc = take(1);
+  s.h3a4 = take((size_t)S.Nk * S.no * 3);
+  s.h3b = take((size_t)S.Nk * S.no * 3);
+  s.acc = take((size_t)S.Nk * S.nb);
+  s.w = take((size_t)S.Nk * S.nb * 3);
+  s.cs = ctx->d_cs + (size_t)side * S.Nk * S.nb * S.no * 6;
+  const cplx<T>* phi = reinterpret_cast<const cplx<T>*>(ctx->d_phi);
+  const cplx<T>* chi = reinterpret_cast<const cplx<T>*>(ctx->d_chi);
+  const cplx<T>* gphi = reinterpret_cast<const cplx<T>*>(ctx->d_gphi);
+  const cplx<T>* gchi = reinterpret_cast<const cplx<T>*>(ctx->d_gchi);
+  s.ket = side == 0 ? phi : chi;
+  s.bra = side == 0 ? chi : phi;
+  s.gket = side == 0 ? gphi : gchi;
+  s.tabV = reinterpret_cast<const T*>(ctx->d_tabV);
+  s.s2b = side == 0 ? T(1) : T(-1);
+  s.side = side;
+}
+
+template <typename T, int N> static Params<T> make_params(tc_ctx* ctx, const double* tw) {
+  Params<T> P{};
+  const auto& S = ctx->S;
+  P.Nk = S.Nk; P.nb = S.nb; P.no = S.no; P.npw_max = S.npw_max; P.ndelta = S.ndelta;
+  P.div = S.prm.div_correction;
+  for (int i = 0; i < 3; ++i)
+    for (int d = 0; d < 3; ++d) P.Bm[i][d] = (T)S.B[i][d];
+  P.invN = (T)(1.0 / ((double)N * N * N));
+  P.Omega = S.Omega;
+  P.invOm2 = 1.0 / (S.Omega * S.Omega);
+  for (int s = 0; s < 2; ++s) { P.corr_c[s] = S.corr_c[s]; P.A[s] = S.prm.A[s]; }
+  for (int t = 0; t < NT; ++t) P.tw[t] = (T)tw[t];
+  P.delta_id = ctx->d_delta_id;
+  P.delta = reinterpret_cast<const T*>(ctx->d_delta);
+  P.tabU = reinterpret_cast<const T*>(ctx->d_tabU);
+  P.tabV = reinterpret_cast<const T*>(ctx->d_tabV);
+  P.hartV = reinterpret_cast<const T*>(ctx->d_hartV);
+  P.hartU = reinterpret_cast<const T*>(ctx->d_hartU);
+  P.hartUs = reinterpret_cast<const T*>(ctx->d_hartUs);
+  P.occ = ctx->d_occ;
+  P.scratch = reinterpret_cast<cplx<T>*>(ctx->d_scratch);
+  fill_side<T, N>(ctx, 0, P.side[0]);
+  fill_side<T, N>(ctx, 1, P.side[1]);
+  return P;
+}
+
+template <typename T, int N> static inline int vol_bytes() { return Geo<N>::vol * (int)sizeof(cplx<T>); }
+template <typename T, int N> static inline int smem_vols(int want, int static_bytes = 1024) {
+  int n = (kSmemLimit - static_bytes) / vol_bytes<T, N>();
+  return n < want ? n : want;
+}
+
+#define TC_SET_SMEM(kern, bytes)                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (bytes)); \
+    if (e_ != cudaSuccess) {                                                                  \
+      ctx->err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e_);              \
+      return TC_ERR_CUDA;                                                                     \
+    }                                                                                         \
+  } while (0)
+
+template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
+  // twiddles exp(-2 pi i j/L) for every codelet length, FP64 host sin/cos
+  static double tw64[2 * kTwTotal];
+  static float tw32[2 * kTwTotal];
+  for (int i = 0, off = 0; i < kNumTwLens; ++i) {
+    const int L = kTwLens[i];
+    for (int j = 0; j < L; ++j) {
+      const double a = -2.0 * 3.14159265358979323846 * j / L;
+      tw64[2 * (off + j)] = std::cos(a);
+      tw64[2 * (off + j) + 1] = std::sin(a);
+      tw32[2 * (off + j)] = (float)std::cos(a);
+      tw32[2 * (off + j) + 1] = (float)std::sin(a);
+    }
+    off += L;
+  }
+  cudaError_t e1 = cudaMemcpyToSymbol(c_tw64, tw64, sizeof(tw64));
+  cudaError_t e2 = cudaMemcpyToSymbol(c_tw32, tw32, sizeof(tw32));
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    ctx->err = "twiddle upload failed";
+    return TC_ERR_CUDA;
+  }
+  const int vb = vol_bytes<T, N>();
+  TC_SET_SMEM((k_orbitals<T, N>), vb);
+  TC_SET_SMEM((k_spec_fwd<T, N>), vb);
+  TC_SET_SMEM((k_hartree_inv<T, N>), vb);
+  TC_SET_SMEM((k_finalize<T, N>), vb);
+  TC_SET_SMEM((k_occ_pairs<T, N>), (smem_vols<T, N>(4) * vb));
+  TC_SET_SMEM((k_pair_chain<T, N>), (smem_vols<T, N>(3) * vb));
+  TC_SET_SMEM((k_pair_3b4<T, N>), (smem_vols<T, N>(2) * vb));
+  TC_SET_SMEM((k_fft3d<T, N, -1>), vb);
+  TC_SET_SMEM((k_fft3d<T, N, +1>), vb);
+  return TC_OK;
+}
+
+template <typename T, int N> size_t scratch_needed(const Setup& S) {
+  const size_t vb = (size_t)vol_bytes<T, N>();
+  const size_t a = (size_t)2 * S.Nk * S.no * 6 * vb;
+  const size_t b = (size_t)2 * S.Nk * S.nb * 3 * vb;
+  return a > b ? a : b;
+}
+
+#define TC_CHECK_LAUNCH(name)                                                                 \
+  do {                                                                                        \
+    cudaError_t e_ = cudaGetLastError();                                                      \
+    if (e_ != cudaSuccess) {                                                                  \
+      ctx->err = std::string(name) + ": " + cudaGetErrorString(e_);                           \
+      return TC_ERR_CUDA;                                                                     \
+    }                                                                                         \
+  } while (0)
+
+// Records the boundary event before stage i (profiling only).
+static inline void stage_mark(tc_ctx* ctx, cudaStream_t st, int i) {
+  if (ctx->profile) cudaEventRecord(ctx->ev[i], st);
+}
+
+static inline int stage_collect(tc_ctx* ctx, int nstages, const int* launches) {
+  if (!ctx->profile) return TC_OK;
+  if (cudaEventSynchronize(ctx->ev[nstages]) != cudaSuccess) {
+    ctx->err = "profiling event wait failed";
+    return TC_ERR_CUDA;
+  }
+  for (int i = 0; i < nstages; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]);
+    ctx->stage_ms[i] += ms;
+    ctx->stage_launch[i] += launches[i];
+  }
+  return TC_OK;
+}
+
+template <typename T, int N>
+int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2* outR, double2* outL,
+                 const double* tw, int nsides, cudaStream_t st) {
+  const auto& S = ctx->S;
+  const int TH = Cfg<N>::threads;
+  const int vb = vol_bytes<T, N>();
+  Params<T> P = make_params<T, N>(ctx, tw);
+  const int nj = S.Nk * S.nb;
+  const int pw_blocks = 2 * 152;
+  int nl[6] = {1, 9, 0, 1, 1, 1};   // kernel launches per stage
+  // 1. orbitals to real space
+  stage_mark(ctx, st, 0);
+  k_orbitals<T, N><<<dim3(nj, 4, 2), TH, vb, st>>>(cphi, cchi, ctx->d_box_index, ctx->d_kpg, S.npw_max, S.nb,
+                                                   (cplx<T>*)ctx->d_phi, (cplx<T>*)ctx->d_chi,
+                                                   (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi);
+  TC_CHECK_LAUNCH("k_orbitals");
+  // 2. densities and Hartree-type fields
+  stage_mark(ctx, st, 1);
+  k_density<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
+  TC_CHECK_LAUNCH("k_density");
+  k_spec_fwd<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 0);
+  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 1);
+  TC_CHECK_LAUNCH("k_spec_fwd");
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 0);
+  k_hartree_inv<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 1);
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 2);
+  k_hartree_inv<T, N><<<dim3(2, nsides), TH, vb, st>>>(P, 5);
+  TC_CHECK_LAUNCH("k_hartree_inv");
+  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 2);
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 3);
+  TC_CHECK_LAUNCH("hartree 3b1");
+  // 3. occupied-pair stage
+  stage_mark(ctx, st, 2);
+  const bool need_a4 = tw[T3A2] != 0 || tw[T3A4] != 0 || tw[T3B2] != 0 || tw[T3B5] != 0;
+  if (need_a4) {
+    Params<T> Pa = P;
+    Pa.nsmem = smem_vols<T, N>(4);
+    k_occ_pairs<T, N><<<dim3(S.Nk * S.no, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
+    TC_CHECK_LAUNCH("k_occ_pairs");
+    k_reduce_a4<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(Pa);
+    TC_CHECK_LAUNCH("k_reduce_a4");
+    k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 3);
+    k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 4);
+    TC_CHECK_LAUNCH("hartree 3b2");
+    nl[2] = 4;
+  }
+  k_vloc<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
+  TC_CHECK_LAUNCH("k_vloc");
+  nl[2] += 1;
+  // 4. pair chains
+  stage_mark(ctx, st, 3);
+  {
+    Params<T> Pc = P;
+    Pc.nsmem = smem_vols<T, N>(3);
+    k_pair_chain<T, N><<<dim3(nj, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
+    TC_CHECK_LAUNCH("k_pair_chain");
+    stage_mark(ctx, st, 4);
+    Params<T> Pb = P;
+    Pb.nsmem = smem_vols<T, N>(2);
+    k_pair_3b4<T, N><<<dim3(nj, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
+    TC_CHECK_LAUNCH("k_pair_3b4");
+  }
+  // 5. local terms, corrections, back to the sphere
+  stage_mark(ctx, st, 5);
+  k_finalize<T, N><<<dim3(nj, nsides), TH, vb, st>>>(P, outR, outL, ctx->d_box_index);
+  TC_CHECK_LAUNCH("k_finalize");
+  stage_mark(ctx, st, 6);
+  return stage_collect(ctx, 6, nl);
+}
+
+template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cudaStream_t st) {
+  const int vb = vol_bytes<T, N>();
+  if (sign < 0)
+    k_fft3d<T, N, -1><<<batch, Cfg<N>::threads, vb, st>>>(reinterpret_cast<cplx<T>*>(data));
+  else
+    k_fft3d<T, N, +1><<<batch, Cfg<N>::threads, vb, st>>>(reinterpret_cast<cplx<T>*>(data));
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+#define TC_INSTANTIATE(T, N)                                                                             \
+  template int run_pipeline<T, N>(tc_ctx*, const double2*, const double2*, double2*, double2*, const double*, \
+                                  int, cudaStream_t);                                                     \
+  template int prepare_kernels<T, N>(tc_ctx*);                                                           \
+  template int run_fft3d<T, N>(void*, int, int, cudaStream_t);                                           \
+  template size_t scratch_needed<T, N>(const Setup&);
+
+}  // namespace tc

@@ -1,0 +1,285 @@
+// Host setup of the TC operator (cell, mesh, spheres, tables), FP64.
+//
+// Conventions: reciprocal rows b_i with a_i . b_j = 2 pi delta_ij; Gamma-centred
+// mesh with fractional coordinates in (-1/2, 1/2]; sphere |k+G|^2/2 <= ecut in
+// lexicographic Miller order; FFT index m of the box stands for the Miller
+// integer m (m <= (n-1)/2) or m - n.
+#include "tc_setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+namespace tc {
+
+static const double kPi = 3.14159265358979323846;
+static const double k4Pi = 4.0 * kPi;
+
+// --- Jastrow kernel transforms (Sec. 2.7.3, Appendix B) -----------------------
+// u~(p) = 4 pi A (1/p^2 - 1/(p^2 + C^-2)) in the cancellation-free form.
+double host_u_tilde(double p2, double A, double C) {
+  const double c2 = 1.0 / (C * C);
+  return k4Pi * A * c2 / (p2 * (p2 + c2));
+}
+
+static double lap_u(double p2, double A, double C) {
+  const double c2 = 1.0 / (C * C);
+  return -k4Pi * A * c2 / (p2 + c2);
+}
+
+// B(g) = -(pi/4) g^2 - (1 + g^2/2) atan(g/2) + (1 + g^2) atan(g) (Appendix B).
+// g <= 1: as printed.  1 < g <= 6: atan(x) = pi/2 - atan(1/x) cancels the pi
+// terms exactly.  g > 6: series in 1/g from the atan Taylor series,
+// B = sum_{k>=1} c_k g^-(2k+1), c_k = (-1)^k [(2^(2k+1)-1)/(2k+1) - (2^(2k+2)-1)/(2k+3)].
+static double B_of_g(double g) {
+  if (g <= 1.0) return -0.25 * kPi * g * g - (1.0 + 0.5 * g * g) * std::atan(0.5 * g) + (1.0 + g * g) * std::atan(g);
+  if (g <= 6.0) return (1.0 + 0.5 * g * g) * std::atan(2.0 / g) - (1.0 + g * g) * std::atan(1.0 / g);
+  const double inv2 = 1.0 / (g * g);
+  double pw = inv2 / g;     // g^-3
+  double sum = 0.0;
+  double p2k1 = 8.0;        // 2^(2k+1) at k = 1
+  for (int k = 1; k < 60; ++k) {
+    const double ck = ((k & 1) ? -1.0 : 1.0) * ((p2k1 - 1.0) / (2 * k + 1) - (2.0 * p2k1 - 1.0) / (2 * k + 3));
+    sum += ck * pw;
+    pw *= inv2;
+    p2k1 *= 4.0;
+    if (std::fabs(ck * pw) < 1e-30 * std::fabs(sum)) break;
+  }
+  return sum;
+}
+
+double host_gradu_sq(double p, double A, double C) {
+  const double g = C * p;
+  if (g == 0.0) return 2.0 * kPi * A * A / C;
+  return k4Pi * A * A / (C * g) * B_of_g(g);
+}
+
+static double V2a(double p2, double A, double C, bool dagger) {
+  const double lap = lap_u(p2, A, C);
+  return k4Pi / p2 + (dagger ? -lap : lap) - host_gradu_sq(std::sqrt(p2), A, C);
+}
+
+// --- small linear algebra ----------------------------------------------------
+static double det3(const double M[3][3]) {
+  return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+         M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+}
+
+static void reciprocal(const double A[3][3], double B[3][3]) {
+  // B = 2 pi (A^-1)^T: rows b_i = 2 pi (a_j x a_k) / det
+  const double d = det3(A);
+  for (int i = 0; i < 3; ++i) {
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    B[i][0] = 2.0 * kPi * (A[j][1] * A[k][2] - A[j][2] * A[k][1]) / d;
+    B[i][1] = 2.0 * kPi * (A[j][2] * A[k][0] - A[j][0] * A[k][2]) / d;
+    B[i][2] = 2.0 * kPi * (A[j][0] * A[k][1] - A[j][1] * A[k][0]) / d;
+  }
+}
+
+static double norm3(const double* v) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+// sum' exp(-alpha p^2)/p^2 over the reciprocal lattice of the supercell (p != 0),
+// until exp(-alpha p^2) < 1e-20; terms summed in ascending order.
+static double aux_sum(const Setup& S, double alpha) {
+  const double pmax = std::sqrt(-std::log(1e-20) / alpha);
+  int bound[3];
+  double Bs[3][3];
+  for (int i = 0; i < 3; ++i) {
+    const double L = norm3(S.A[i]) * S.prm.kmesh[i];
+    bound[i] = (int)std::ceil(pmax * L / (2.0 * kPi)) + 1;
+    for (int d = 0; d < 3; ++d) Bs[i][d] = S.B[i][d] / S.prm.kmesh[i];
+  }
+  std::vector<double> w;
+  for (int a = -bound[0]; a <= bound[0]; ++a)
+    for (int b = -bound[1]; b <= bound[1]; ++b)
+      for (int c = -bound[2]; c <= bound[2]; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        double p[3];
+        for (int d = 0; d < 3; ++d) p[d] = a * Bs[0][d] + b * Bs[1][d] + c * Bs[2][d];
+        const double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        w.push_back(std::exp(-alpha * p2) / p2);
+      }
+  std::sort(w.begin(), w.end());
+  double s = 0.0;
+  for (double x : w) s += x;
+  return s;
+}
+
+static int fft_rep(int m, int n) { return m <= (n - 1) / 2 ? m : m - n; }
+
+std::string build_setup(const tc_params& p, Setup& S) {
+  S.prm = p;
+  if (p.fft[0] != p.fft[1] || p.fft[1] != p.fft[2]) return "unsupported: FFT box must be cubic";
+  const int n = p.fft[0];
+  if (!(n == 9 || n == 12 || n == 15 || n == 16 || n == 24)) return "unsupported: FFT box size (9, 12, 15, 16 or 24)";
+  for (int i = 0; i < 3; ++i)
+    if (p.kmesh[i] < 1 || p.kmesh[i] > 16) return "kmesh entries must be in [1, 16]";
+  if (!(p.nocc > 0 && p.nocc <= p.nbands)) return "need 0 < nocc <= nbands";
+  if (!(p.ecut_ha > 0)) return "ecut_ha must be positive";
+  if (!(p.C[0] > 0 && p.C[1] > 0)) return "Jastrow C must be positive";
+  if (!(p.A[0] >= 0 && p.A[1] >= 0)) return "Jastrow A must be non-negative";
+  if (p.precision != TC_FP64 && p.precision != TC_FP32) return "precision must be TC_FP64 or TC_FP32";
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) S.A[i][j] = p.lattice[i][j];
+  S.Omega = std::fabs(det3(S.A));
+  if (!(S.Omega > 0)) return "lattice is singular";
+  reciprocal(S.A, S.B);
+  S.n = n;
+  S.N = n * n * n;
+  S.nb = p.nbands;
+  S.no = p.nocc;
+  S.Nk = p.kmesh[0] * p.kmesh[1] * p.kmesh[2];
+
+  // k mesh
+  S.kfrac.clear();
+  S.kcart.clear();
+  for (int a = 0; a < p.kmesh[0]; ++a)
+    for (int b = 0; b < p.kmesh[1]; ++b)
+      for (int c = 0; c < p.kmesh[2]; ++c) {
+        const int idx[3] = {a, b, c};
+        std::array<double, 3> f{};
+        for (int i = 0; i < 3; ++i) {
+          f[i] = (double)idx[i] / p.kmesh[i];
+          if (f[i] > 0.5) f[i] -= 1.0;
+        }
+        std::array<double, 3> kc{};
+        for (int d = 0; d < 3; ++d) kc[d] = f[0] * S.B[0][d] + f[1] * S.B[1][d] + f[2] * S.B[2][d];
+        S.kfrac.push_back(f);
+        S.kcart.push_back(kc);
+      }
+
+  // spheres
+  S.miller.assign(S.Nk, {});
+  S.npw.assign(S.Nk, 0);
+  for (int k = 0; k < S.Nk; ++k) {
+    const double gmax = std::sqrt(2.0 * p.ecut_ha) + norm3(S.kcart[k].data());
+    int bound[3];
+    for (int i = 0; i < 3; ++i) bound[i] = (int)std::ceil(gmax * norm3(S.A[i]) / (2.0 * kPi)) + 1;
+    for (int a = -bound[0]; a <= bound[0]; ++a)
+      for (int b = -bound[1]; b <= bound[1]; ++b)
+        for (int c = -bound[2]; c <= bound[2]; ++c) {
+          double kg[3];
+          for (int d = 0; d < 3; ++d) kg[d] = S.kcart[k][d] + (a * S.B[0][d] + b * S.B[1][d] + c * S.B[2][d]);
+          if (0.5 * (kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]) <= p.ecut_ha) S.miller[k].push_back({a, b, c});
+        }
+    S.npw[k] = (int)S.miller[k].size();
+    for (auto& m : S.miller[k])
+      for (int i = 0; i < 3; ++i)
+        if (std::abs(m[i]) > (n - 1) / 2) return "plane-wave sphere does not fit the FFT box";
+  }
+  S.npw_max = *std::max_element(S.npw.begin(), S.npw.end());
+  S.miller_flat.assign((size_t)S.Nk * S.npw_max * 3, 0);
+  S.box_index.assign((size_t)S.Nk * S.npw_max, -1);
+  for (int k = 0; k < S.Nk; ++k)
+    for (int g = 0; g < S.npw[k]; ++g) {
+      const auto& m = S.miller[k][g];
+      for (int i = 0; i < 3; ++i) S.miller_flat[((size_t)k * S.npw_max + g) * 3 + i] = m[i];
+      const int i1 = (m[0] + n) % n, i2 = (m[1] + n) % n, i3 = (m[2] + n) % n;
+      S.box_index[(size_t)k * S.npw_max + g] = (i1 * n + i2) * n + i3;
+    }
+
+  // divergence-correction constant (Eq. correction2, k on the mesh)
+  if (p.alpha > 0) {
+    S.alpha = p.alpha;
+  } else {
+    double best = 1e300, Sup[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int d = 0; d < 3; ++d) Sup[i][d] = S.A[i][d] * p.kmesh[i];
+    for (int a = -2; a <= 2; ++a)
+      for (int b = -2; b <= 2; ++b)
+        for (int c = -2; c <= 2; ++c) {
+          if (!a && !b && !c) continue;
+          double v[3];
+          for (int d = 0; d < 3; ++d) v[d] = a * Sup[0][d] + b * Sup[1][d] + c * Sup[2][d];
+          best = std::min(best, norm3(v));
+        }
+    S.alpha = (best / 12.0) * (best / 12.0);
+  }
+  S.Gamma0 = S.Omega / (4.0 * std::sqrt(kPi * kPi * kPi * S.alpha)) - (-S.alpha + aux_sum(S, S.alpha)) / S.Nk;
+  for (int s = 0; s < 2; ++s) {
+    const double A = p.A[s], C = p.C[s];
+    S.corr_c[s] = (k4Pi * A) * (k4Pi * A) * S.Gamma0 + p.ushort_factor * k4Pi * A * (-k4Pi * A * C * C) / S.Nk;
+  }
+
+  // distinct Delta = k_out - k_part
+  std::map<std::tuple<long, long, long>, int> ids;
+  S.delta_id.assign((size_t)S.Nk * S.Nk, 0);
+  S.delta.clear();
+  for (int ko = 0; ko < S.Nk; ++ko)
+    for (int kp = 0; kp < S.Nk; ++kp) {
+      long key[3];
+      for (int i = 0; i < 3; ++i) key[i] = std::lround((S.kfrac[ko][i] - S.kfrac[kp][i]) * p.kmesh[i]);
+      auto t = std::make_tuple(key[0], key[1], key[2]);
+      auto it = ids.find(t);
+      int id;
+      if (it == ids.end()) {
+        id = (int)S.delta.size();
+        ids[t] = id;
+        std::array<double, 3> dc{};
+        for (int d = 0; d < 3; ++d) dc[d] = S.kcart[ko][d] - S.kcart[kp][d];
+        S.delta.push_back(dc);
+      } else {
+        id = it->second;
+      }
+      S.delta_id[(size_t)ko * S.Nk + kp] = id;
+    }
+  S.ndelta = (int)S.delta.size();
+
+  // tables
+  const size_t N = S.N;
+  S.tabV.assign((size_t)S.ndelta * 2 * N, 0.0);
+  S.tabU.assign((size_t)S.ndelta * 2 * N, 0.0);
+  const double vj0 = -k4Pi * p.A[0] - 2.0 * kPi * p.A[0] * p.A[0] / p.C[0];   // finite Jastrow part at p = 0
+  const double v0 = (vj0 + (p.div_correction ? k4Pi * S.Nk * S.Gamma0 : 0.0)) / S.Omega;
+  for (int id = 0; id < S.ndelta; ++id)
+    for (int i1 = 0; i1 < n; ++i1)
+      for (int i2 = 0; i2 < n; ++i2)
+        for (int i3 = 0; i3 < n; ++i3) {
+          const int r1 = fft_rep(i1, n), r2 = fft_rep(i2, n), r3 = fft_rep(i3, n);
+          double pv[3];
+          for (int d = 0; d < 3; ++d) pv[d] = S.delta[id][d] + (r1 * S.B[0][d] + r2 * S.B[1][d] + r3 * S.B[2][d]);
+          const double p2 = pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2];
+          const size_t g = ((size_t)i1 * n + i2) * n + i3;
+          double* V = &S.tabV[(size_t)id * 2 * N];
+          double* U = &S.tabU[(size_t)id * 2 * N];
+          if (p2 == 0.0) {
+            V[g] = v0;
+            V[N + g] = v0;   // the adjoint of the discrete right operator keeps V_2a(0)
+            U[g] = 0.0;
+            U[N + g] = 0.0;
+          } else {
+            V[g] = V2a(p2, p.A[0], p.C[0], false) / S.Omega;
+            V[N + g] = V2a(p2, p.A[0], p.C[0], true) / S.Omega;
+            U[g] = host_u_tilde(p2, p.A[0], p.C[0]) / S.Omega;
+            U[N + g] = host_u_tilde(p2, p.A[1], p.C[1]) / S.Omega;
+          }
+        }
+  S.hartV.assign(2 * N, 0.0);
+  S.hartU.assign(N, 0.0);
+  S.hartUs.assign(2 * N, 0.0);
+  for (int i1 = 0; i1 < n; ++i1)
+    for (int i2 = 0; i2 < n; ++i2)
+      for (int i3 = 0; i3 < n; ++i3) {
+        const size_t g = ((size_t)i1 * n + i2) * n + i3;
+        if (g == 0) continue;
+        const int r1 = fft_rep(i1, n), r2 = fft_rep(i2, n), r3 = fft_rep(i3, n);
+        double G[3];
+        for (int d = 0; d < 3; ++d) G[d] = r1 * S.B[0][d] + r2 * S.B[1][d] + r3 * S.B[2][d];
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        double vr = 0, vl = 0, u = 0;
+        for (int s = 0; s < 2; ++s) {
+          vr += V2a(g2, p.A[s], p.C[s], false);
+          vl += V2a(g2, p.A[s], p.C[s], true);
+          const double us = host_u_tilde(g2, p.A[s], p.C[s]);
+          u += us;
+          S.hartUs[(size_t)s * N + g] = us;
+        }
+        S.hartV[g] = vr / S.Omega;
+        S.hartV[N + g] = vl / S.Omega;
+        S.hartU[g] = u / S.Omega;
+      }
+  return "";
+}
+
+}  // namespace tc

@@ -1,0 +1,45 @@
+// Host-side setup of the TC operator: cell, k mesh, plane-wave spheres, FFT
+// box maps, the divergence-correction constant and the FP64 kernel tables.
+#pragma once
+#include <array>
+#include <string>
+#include <vector>
+
+#include "../../include/tc.h"
+
+namespace tc {
+
+struct Setup {
+  tc_params prm{};
+  double A[3][3]{};        // lattice rows a_i
+  double B[3][3]{};        // reciprocal rows b_i, a_i . b_j = 2 pi delta_ij
+  double Omega = 0.0;
+  int Nk = 0, n = 0, N = 0, nb = 0, no = 0;
+  std::vector<std::array<double, 3>> kfrac, kcart;
+  std::vector<std::vector<std::array<int, 3>>> miller;   // per k, lexicographic
+  std::vector<int> npw;
+  int npw_max = 0;
+  std::vector<int> miller_flat;                          // [Nk][npw_max][3], zero padded
+  std::vector<int> box_index;                            // [Nk][npw_max], -1 padded
+  double alpha = 0.0, Gamma0 = 0.0;
+  // distinct Delta = k_out - k_part (unreduced)
+  int ndelta = 0;
+  std::vector<int> delta_id;                             // [Nk][Nk]
+  std::vector<std::array<double, 3>> delta;              // Cartesian
+  // FP64 tables, all divided by Omega, over the box in global (unpadded) order
+  std::vector<double> tabV;    // [ndelta][2][N]  V_2a (right), V_2a^dagger (left), p = 0 value incl. correction
+  std::vector<double> tabU;    // [ndelta][2][N]  u~_pp, u~_ap (0 at p = 0)
+  std::vector<double> hartV;   // [2][N]          (V_pp + V_ap)(G) right / left, 0 at G = 0
+  std::vector<double> hartU;   // [N]             (u~pp + u~ap)(G), 0 at G = 0
+  std::vector<double> hartUs;  // [2][N]          u~_s(G) (NOT divided by Omega), 0 at G = 0
+  double corr_c[2]{};          // (4 pi A_s)^2 Gamma0 + x 4 pi A_s u_short,s / Nk
+};
+
+// Returns an empty string on success, otherwise the reason.
+std::string build_setup(const tc_params& p, Setup& S);
+
+// Appendix B kernel pieces (host, FP64), exposed for the table tests.
+double host_u_tilde(double p2, double A, double C);
+double host_gradu_sq(double p, double A, double C);
+
+}  // namespace tc

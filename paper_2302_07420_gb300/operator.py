@@ -1,0 +1,144 @@
+"""Python front end of the C ABI: tc_init / tc_layout / tc_apply / tc_energy.
+
+Device memory and streams come from PyTorch; every computation runs in
+libtc.so.  Orbital arrays are complex128 tensors of shape (Nk, nbands,
+npw_max) in the layout of ``Context.layout()``.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Context:
+    """One tc_init context (owns the library's tables and workspace)."""
+
+    def __init__(self, lattice, kmesh, ecut, fft, nbands, nocc, A, C, alpha=0.0, div_correction=1,
+                 ushort_factor=1.0, precision="fp64", term_mask=0):
+        self.lib = _lib.load()
+        self.params = _lib.make_params(lattice, kmesh, ecut, fft, nbands, nocc, A, C, alpha, div_correction,
+                                       ushort_factor, precision, term_mask)
+        h = ctypes.c_void_p()
+        st = self.lib.tc_init(ctypes.byref(self.params), ctypes.byref(h))
+        if st != _lib.TC_OK:
+            msg = self.lib.tc_last_error(None)
+            raise _lib.TCError(st, msg.decode() if msg else "tc_init failed")
+        self.h = h
+        self.nbands, self.nocc = int(nbands), int(nocc)
+        nk, npw_max = ctypes.c_int(), ctypes.c_int()
+        pn = ctypes.POINTER(ctypes.c_int)()
+        pm = ctypes.POINTER(ctypes.c_int)()
+        _lib.check(self.lib, self.h, self.lib.tc_layout(self.h, ctypes.byref(nk), ctypes.byref(npw_max),
+                                                        ctypes.byref(pn), ctypes.byref(pm)))
+        self.nk, self.npw_max = nk.value, npw_max.value
+        self.npw = np.ctypeslib.as_array(pn, shape=(self.nk,)).copy()
+        self.miller = np.ctypeslib.as_array(pm, shape=(self.nk, self.npw_max, 3)).copy()
+        sc = (ctypes.c_double * 4)()
+        _lib.check(self.lib, self.h, self.lib.tc_setup_scalars(self.h, sc))
+        self.Omega, self.alpha, self.Gamma0, self.ndelta = sc[0], sc[1], sc[2], int(sc[3])
+
+    def layout(self):
+        return self.npw, self.miller
+
+    def _occ(self, occ):
+        occ = np.ascontiguousarray(np.asarray(occ, dtype=np.float64).reshape(self.nk, self.nbands))
+        return occ, occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def _check_orbitals(self, x):
+        shape = (self.nk, self.nbands, self.npw_max)
+        if tuple(x.shape) != shape:
+            raise ValueError("orbital array must have shape %s" % (shape,))
+        return x
+
+    def apply(self, phi_R, phi_L, occ, out_R=None, out_L=None, stream=None):
+        """(out_R, out_L) = operator applied to every right / left orbital (torch, cuda)."""
+        import torch
+        phi_R = self._check_orbitals(phi_R).contiguous()
+        phi_L = self._check_orbitals(phi_L).contiguous()
+        if phi_R.dtype != torch.complex128 or phi_L.dtype != torch.complex128:
+            raise TypeError("orbitals must be complex128")
+        if out_R is None:
+            out_R = torch.empty_like(phi_R)
+        if out_L is None:
+            out_L = torch.empty_like(phi_L)
+        occ_np, occ_p = self._occ(occ)
+        st = self.lib.tc_apply(self.h, _ptr(phi_R), _ptr(phi_L), occ_p, _ptr(out_R), _ptr(out_L),
+                               _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return out_R, out_L
+
+    def apply_host(self, phi_R, phi_L, occ, stream=None):
+        """Host arrays in and out (numpy complex128): the copies run inside the call."""
+        phi_R = np.ascontiguousarray(self._check_orbitals(phi_R), dtype=np.complex128)
+        phi_L = np.ascontiguousarray(self._check_orbitals(phi_L), dtype=np.complex128)
+        out_R = np.empty_like(phi_R)
+        out_L = np.empty_like(phi_L)
+        occ_np, occ_p = self._occ(occ)
+        vp = ctypes.c_void_p
+        st = self.lib.tc_apply(self.h, vp(phi_R.ctypes.data), vp(phi_L.ctypes.data), occ_p,
+                               vp(out_R.ctypes.data), vp(out_L.ctypes.data), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return out_R, out_L
+
+    def energy(self, phi_R, phi_L, occ, terms=False, stream=None):
+        """TC pseudo-energy per cell; with terms=True also the per-term dict."""
+        import torch
+        phi_R = self._check_orbitals(phi_R).contiguous()
+        phi_L = self._check_orbitals(phi_L).contiguous()
+        occ_np, occ_p = self._occ(occ)
+        E = ctypes.c_double()
+        Et = (ctypes.c_double * _lib.TC_NTERMS)() if terms else None
+        st = self.lib.tc_energy(self.h, _ptr(phi_R), _ptr(phi_L), occ_p, ctypes.byref(E),
+                                Et if terms else None, _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        if not terms:
+            return E.value
+        d = {t: Et[i] for i, t in enumerate(_lib.TERMS)}
+        d["kin"] = Et[16]
+        return E.value, d
+
+    def profile(self, enable=True):
+        """Enable (and reset) or disable per-stage device timing."""
+        _lib.check(self.lib, self.h, self.lib.tc_profile(self.h, 1 if enable else 0))
+
+    def stage_times(self):
+        """{stage: (accumulated ms, kernel launches)} since profile(True)."""
+        ms = (ctypes.c_double * _lib.TC_NSTAGES)()
+        nl = (ctypes.c_int * _lib.TC_NSTAGES)()
+        _lib.check(self.lib, self.h, self.lib.tc_stage_times(self.h, ms, nl, _lib.TC_NSTAGES))
+        return {s: (ms[i], nl[i]) for i, s in enumerate(_lib.STAGES)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft3d(x, sign, stream=None):
+    """In-place batched 3D FFT of a (batch, n, n, n) complex cuda tensor with the library's kernel."""
+    import torch
+    lib = _lib.load()
+    n = x.shape[-1]
+    prec = _lib.TC_FP64 if x.dtype == torch.complex128 else _lib.TC_FP32
+    batch = int(np.prod(x.shape[:-3])) if x.dim() > 3 else 1
+    st = lib.tc_fft3d(n, prec, int(sign), _ptr(x), batch, _stream_handle(stream))
+    _lib.check(lib, None, st)
+    return x

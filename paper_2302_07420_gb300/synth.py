@@ -11,8 +11,8 @@ Workloads (all in Hartree atomic units):
   Gamma only, FFT box 16^3, sphere |n|^2 <= 16; chi = phi.
 * ``si_k444``  -- silicon-like FCC cell, a = 10.26 bohr, 8 electrons (4 occupied
   bands per k), 4x4x4 Gamma-centred mesh, ecut = 7.5 Ha (15 Ry), box 24^3.
-  Coefficients (N(0,1) + i N(0,1))/sqrt(2) exp(-|k+G|^2/4), QR-orthonormalised per
-  k; chi = X' (Phi^H X')^{-1} with X' = Phi + 1e-2 R (R drawn the same way,
+  Coefficients (N(0,1) + i N(0,1))/sqrt(2) exp(-|k+G|^2/4), orthonormalised per
+  k by modified Gram-Schmidt (band order); chi = X' (Phi^H X')^{-1} with X' = Phi + 1e-2 R (R drawn the same way,
   column-normalised), so chi^H phi = I and <phi_i|phi_i> = 1.
 * ``heg_114``  -- HEG, N = 114 electrons (57 plane waves, |n|^2 <= 5), r_s = 2,
   Gamma only, box 48^3, sphere |n|^2 <= 144.
@@ -77,6 +77,16 @@ def _gauss_coeffs(rng, kpg, npw_max, nbands):
     return c * damp[:, None]
 
 
+def _gram_schmidt(P):
+    """Modified Gram-Schmidt on the columns (platform-independent signs)."""
+    P = P.copy()
+    for b in range(P.shape[1]):
+        for a in range(b):
+            P[:, b] -= np.vdot(P[:, a], P[:, b]) * P[:, a]
+        P[:, b] /= np.linalg.norm(P[:, b])
+    return P
+
+
 def random_orbitals(seed, kpg_list, npw_max, nbands, perturb=1e-2):
     """(c_phi, c_chi) of shape (Nk, nbands, npw_max), biorthonormal per k.
 
@@ -88,8 +98,7 @@ def random_orbitals(seed, kpg_list, npw_max, nbands, perturb=1e-2):
     c_chi = np.zeros_like(c_phi)
     for k, kpg in enumerate(kpg_list):
         npw = kpg.shape[0]
-        P = _gauss_coeffs(rng, kpg, npw_max, nbands)
-        P, _ = np.linalg.qr(P)
+        P = _gram_schmidt(_gauss_coeffs(rng, kpg, npw_max, nbands))
         R = _gauss_coeffs(rng, kpg, npw_max, nbands)
         R = R / np.linalg.norm(R, axis=0, keepdims=True)
         Xp = P + perturb * R

@@ -1,0 +1,71 @@
+"""Writes oracle expected values for the full-size workloads (calls only oracle/).
+
+si_k444: silicon-like FCC cell, a = 10.26 bohr, 4x4x4 mesh, ecut 7.5 Ha, box 24^3,
+4 occupied bands, inputs from paper_2302_07420_gb300.synth (seed 230207420 + 1).
+Stored: out_R / out_L (every term summed) at the sampled k-points, E_TC and its
+per-term split, and a few input coefficients to confirm that the regenerated
+inputs are the ones used here.
+
+Run:  python tests/golden/make_golden.py si_k444
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from oracle import operator as OP  # noqa: E402
+from oracle.cell import Setup  # noqa: E402
+from paper_2302_07420_gb300 import synth  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SAMPLE_K = {"si_k444": [0, 21, 42]}
+SEED_OFFSET = {"si_k444": 1}
+
+
+def inputs(name):
+    p = synth.WORKLOADS[name]()
+    S = Setup(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"])
+    c_phi, c_chi = synth.random_orbitals(synth.SEED0 + SEED_OFFSET[name], [S.kpG(k) for k in range(S.Nk)],
+                                         S.npw_max, S.nbands)
+    occ = synth.occupations(S.Nk, S.nbands, S.nocc)
+    return p, S, c_phi, c_chi, occ
+
+
+def cplx_list(a):
+    return [[float(x.real), float(x.imag)] for x in np.asarray(a).ravel()]
+
+
+def main(name):
+    t0 = time.time()
+    p, S, c_phi, c_chi, occ = inputs(name)
+    ks = SAMPLE_K[name]
+    right = OP.apply_operator(S, c_phi, c_chi, occ, left=False)            # all k: needed for E
+    E = OP.energy_terms(S, c_phi, c_chi, occ, res=right)
+    left = OP.apply_operator(S, c_phi, c_chi, occ, left=True, kpoints=ks)
+    out_r, out_l = OP.total(right), OP.total(left)
+    doc = {
+        "workload": name,
+        "source": "oracle/ (tests/golden/make_golden.py)",
+        "seed": synth.SEED0 + SEED_OFFSET[name],
+        "shape": [S.Nk, S.nbands, S.npw_max],
+        "sample_k": ks,
+        "input_probe": {"index": [[k, b, 5] for k in ks for b in range(S.nbands)],
+                        "phi": cplx_list([c_phi[k, b, 5] for k in ks for b in range(S.nbands)]),
+                        "chi": cplx_list([c_chi[k, b, 5] for k in ks for b in range(S.nbands)])},
+        "out_R": {str(k): cplx_list(out_r[k]) for k in ks},
+        "out_L": {str(k): cplx_list(out_l[k]) for k in ks},
+        "energy": E,
+        "oracle_seconds": time.time() - t0,
+    }
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(doc, f)
+    print("wrote", name, "in %.0f s" % (time.time() - t0))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "si_k444")

@@ -1,0 +1,195 @@
+"""GPU path vs the FP64 oracle through the C ABI (parity tests proper).
+
+Tolerances: FP64 path <= 1e-11 relative (max over coefficients, relative to
+the largest output coefficient); FP32 path <= 1e-5 relative (operator output),
+the bound stated for the reduced-precision path.
+"""
+import numpy as np
+import pytest
+
+from conftest import make_setup
+from oracle import operator as OP
+from paper_2302_07420_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-11
+TOL32 = 1e-5
+
+
+def _ctx(p, **kw):
+    from paper_2302_07420_gb300.operator import Context
+    args = dict(lattice=p["lattice"], kmesh=p["kmesh"], ecut=p["ecut"], fft=p["fft"], nbands=p["nbands"],
+                nocc=p["nocc"], A=p["A"], C=p["C"])
+    args.update(kw)
+    return Context(**args)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda")
+
+
+def tiny_case(seed, kmesh, fft, nbands=3, nocc=2, fill=None, ecut=1.6, scale=5.0):
+    p = synth.tiny_params(seed, kmesh=kmesh, fft=(fft,) * 3, ecut=ecut, nbands=nbands, nocc=nocc, scale=scale)
+    S = make_setup(p)
+    c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 200 + seed, [S.kpG(k) for k in range(S.Nk)], S.npw_max,
+                                         S.nbands, perturb=0.1)
+    occ = synth.occupations(S.Nk, S.nbands, S.nocc)
+    if fill is not None:
+        occ[:, :nocc] = np.asarray(fill)[None]
+    return p, S, c_phi, c_chi, occ
+
+
+@pytest.mark.parametrize("n", [9, 12, 15, 16, 24])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_fft3d_matches_numpy(n, prec, sign):
+    from paper_2302_07420_gb300.operator import fft3d
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((3, n, n, n)) + 1j * rng.standard_normal((3, n, n, n))
+    ref = np.fft.fftn(x, axes=(1, 2, 3)) if sign < 0 else np.fft.ifftn(x, axes=(1, 2, 3)) * n ** 3
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    y = torch.from_numpy(x).to(dt).cuda()
+    fft3d(y, sign)
+    torch.cuda.synchronize()
+    err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err < (1e-14 if prec == "fp64" else 2e-6), err
+
+
+@pytest.mark.parametrize("name", ["heg_14", "si_k444", "heg_114"])
+def test_layout_matches_oracle(name):
+    p = synth.WORKLOADS[name]()
+    if p["fft"][0] not in (9, 12, 15, 16, 24):
+        pytest.skip("box size not compiled")
+    S = make_setup(p)
+    ctx = _ctx(p)
+    npw, miller = ctx.layout()
+    assert npw.tolist() == S.npw.tolist()
+    for k in range(S.Nk):
+        assert np.array_equal(miller[k, : S.npw[k]], S.miller[k])
+    assert abs(ctx.Gamma0 - S.Gamma0) < 1e-12 * abs(S.Gamma0)
+    assert abs(ctx.alpha - S.alpha) < 1e-14 * S.alpha
+    ctx.close()
+
+
+CASES = [(0, (1, 1, 2), 9), (1, (2, 1, 1), 12), (2, (1, 2, 2), 15)]
+
+
+@pytest.mark.parametrize("seed,kmesh,fft", CASES)
+def test_parity_fp64_every_term(seed, kmesh, fft):
+    p, S, c_phi, c_chi, occ = tiny_case(seed, kmesh, fft, fill=(1.0, 0.6))
+    ref_r = OP.apply_operator(S, c_phi, c_chi, occ, left=False)
+    ref_l = OP.apply_operator(S, c_phi, c_chi, occ, left=True)
+    scale = max(np.abs(OP.total(ref_r)).max(), np.abs(OP.total(ref_l)).max())
+    for t_i, t in enumerate(OP.TERMS):
+        ctx = _ctx(p, term_mask=1 << t_i)
+        out_r, out_l = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+        torch.cuda.synchronize()
+        er = np.abs(out_r.cpu().numpy() - ref_r[t]).max() / scale
+        el = np.abs(out_l.cpu().numpy() - ref_l[t]).max() / scale
+        ctx.close()
+        assert er < TOL64 and el < TOL64, (t, er, el)
+
+
+@pytest.mark.parametrize("seed,kmesh,fft", CASES)
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_parity_total(seed, kmesh, fft, prec, tol):
+    p, S, c_phi, c_chi, occ = tiny_case(seed, kmesh, fft, fill=(1.0, 0.6))
+    ref_r, ref_l = OP.tc_apply(S, c_phi, c_chi, occ)
+    ctx = _ctx(p, precision=prec)
+    out_r, out_l = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+    torch.cuda.synchronize()
+    scale = max(np.abs(ref_r).max(), np.abs(ref_l).max())
+    er = np.abs(out_r.cpu().numpy() - ref_r).max() / scale
+    el = np.abs(out_l.cpu().numpy() - ref_l).max() / scale
+    ctx.close()
+    assert er < tol and el < tol, (er, el)
+
+
+def test_parity_heg_14_fp64():
+    p = synth.WORKLOADS["heg_14"]()
+    S = make_setup(p)
+    c = synth.heg_orbitals(S.miller[0], S.npw_max, 1)
+    occ = synth.occupations(1, S.nbands, S.nocc)
+    ref_r, ref_l = OP.tc_apply(S, c, c, occ)
+    ctx = _ctx(p)
+    out_r, out_l = ctx.apply(_dev(c), _dev(c), occ)
+    torch.cuda.synchronize()
+    scale = np.abs(ref_r).max()
+    assert np.abs(out_r.cpu().numpy() - ref_r).max() / scale < TOL64
+    assert np.abs(out_l.cpu().numpy() - ref_l).max() / scale < TOL64
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_energy_and_terms(prec, tol):
+    p, S, c_phi, c_chi, occ = tiny_case(1, (2, 1, 1), 12)
+    ref = OP.energy_terms(S, c_phi, c_chi, occ)
+    ctx = _ctx(p, precision=prec)
+    E, Et = ctx.energy(_dev(c_phi), _dev(c_chi), occ, terms=True)
+    ctx.close()
+    scale = max(abs(ref["total"]), max(abs(v) for v in ref.values()))
+    assert abs(E - ref["total"]) < tol * scale, (E, ref["total"])
+    for t in OP.TERMS + ("kin",):
+        assert abs(Et[t] - ref[t]) < tol * scale, (t, Et[t], ref[t])
+
+
+def test_host_pointers_equal_device_pointers():
+    p, S, c_phi, c_chi, occ = tiny_case(0, (1, 1, 2), 9)
+    ctx = _ctx(p)
+    dr, dl = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+    torch.cuda.synchronize()
+    hr, hl = ctx.apply_host(c_phi, c_chi, occ)
+    ctx.close()
+    assert np.array_equal(hr, dr.cpu().numpy()) and np.array_equal(hl, dl.cpu().numpy())
+
+
+def test_error_paths():
+    from paper_2302_07420_gb300 import _lib
+    p = synth.tiny_params(0, kmesh=(1, 1, 2), fft=(9, 9, 9), ecut=1.6, scale=5.0)
+    with pytest.raises(_lib.TCError) as e:
+        _ctx(p, fft=(10, 10, 10))
+    assert e.value.status == _lib.TC_ERR_UNSUPPORTED
+    with pytest.raises(_lib.TCError) as e:
+        _ctx(p, nocc=5)
+    assert e.value.status == _lib.TC_ERR_ARG
+    with pytest.raises(_lib.TCError) as e:
+        _ctx(p, ecut=50.0)          # sphere no longer fits the 9^3 box
+    assert e.value.status == _lib.TC_ERR_ARG
+    ctx = _ctx(p)
+    lib = ctx.lib
+    import ctypes
+    occ = np.ones(ctx.nk * ctx.nbands)
+    st = lib.tc_apply(ctx.h, None, None, occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, None, None)
+    assert st == _lib.TC_ERR_ARG
+    bad = -occ
+    x = torch.zeros((ctx.nk, ctx.nbands, ctx.npw_max), dtype=torch.complex128, device="cuda")
+    with pytest.raises(_lib.TCError) as e:
+        ctx.apply(x, x, bad)
+    assert e.value.status == _lib.TC_ERR_ARG
+    ctx.close()
+    assert lib.tc_destroy(None) == _lib.TC_ERR_STATE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_repeated_calls_in_one_context_are_identical(prec):
+    """State left by one call (workspace, padding) must not leak into the next."""
+    p, S, c_phi, c_chi, occ = tiny_case(1, (2, 1, 1), 12)
+    ctx = _ctx(p, precision=prec)
+    outs = []
+    for mask in (0, 1 << 7, 0):          # full, then 3a2 only, then full again
+        ctx.params.term_mask = mask
+        ctx.lib.tc_destroy(ctx.h)
+        import ctypes
+        h = ctypes.c_void_p()
+        assert ctx.lib.tc_init(ctypes.byref(ctx.params), ctypes.byref(h)) == 0
+        ctx.h = h
+        for _ in range(2):
+            r, l = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+            torch.cuda.synchronize()
+            outs.append((mask, r.cpu().numpy(), l.cpu().numpy()))
+    ctx.close()
+    for a, b in zip(outs[0::2], outs[1::2]):
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    assert np.array_equal(outs[0][1], outs[4][1])
