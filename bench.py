@@ -156,6 +156,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="si_k444", choices=["si_k444", "si_k222"],
+                    help="si_k222 (2x2x2 mesh) is the small case used for ncu captures")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="FP32 applies only (warm-up + steps), no JSON line: the ncu capture command")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -173,7 +177,7 @@ def main():
     from paper_2302_07420_gb300 import synth
     from paper_2302_07420_gb300.operator import Context
 
-    p = synth.WORKLOADS["si_k444"]()
+    p = synth.WORKLOADS["si_k444"]() if args.workload == "si_k444" else synth.si_params(kmesh=(2, 2, 2))
     ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
                   precision="fp32")
     npw, miller = ctx.layout()
@@ -196,6 +200,12 @@ def main():
     for _ in range(args.warmup):
         ctx.apply(d_phi, d_chi, occ, out_r, out_l)
     barrier()
+    if args.profile_run:
+        for _ in range(args.steps):
+            ctx.apply(d_phi, d_chi, occ, out_r, out_l)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     ctx.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:

@@ -1,0 +1,59 @@
+"""Full-size parity: silicon-like 4x4x4 / 24^3 workload vs oracle values at sampled k-points.
+
+The expected values were written by tests/golden/make_golden.py (oracle only);
+the inputs are regenerated from the same seed and checked against the stored
+probe coefficients first.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from conftest import make_setup
+from paper_2302_07420_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def golden():
+    g = json.load(open(os.path.join(HERE, "golden", "si_k444.json")))
+    p = synth.WORKLOADS["si_k444"]()
+    S = make_setup(p)
+    c_phi, c_chi = synth.random_orbitals(g["seed"], [S.kpG(k) for k in range(S.Nk)], S.npw_max, S.nbands)
+    probe = np.array([c_phi[k, b, i] for k, b, i in g["input_probe"]["index"]])
+    ref_probe = np.array(g["input_probe"]["phi"]).view(complex).ravel()
+    assert np.abs(probe - ref_probe).max() < 1e-13, "regenerated inputs differ from the golden inputs"
+    occ = synth.occupations(S.Nk, S.nbands, S.nocc)
+    return g, p, S, c_phi, c_chi, occ
+
+
+def _ref(g, key, k, nb):
+    return np.array(g[key][str(k)]).view(complex).reshape(nb, -1)
+
+
+@pytest.mark.parametrize("prec,tol,etol", [("fp64", 1e-11, 1e-11), ("fp32", 1e-5, 1e-6)])
+def test_full_size_sampled_outputs_and_energy(golden, prec, tol, etol):
+    from paper_2302_07420_gb300.operator import Context
+    g, p, S, c_phi, c_chi, occ = golden
+    ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                  precision=prec)
+    d_phi = torch.from_numpy(c_phi).cuda()
+    d_chi = torch.from_numpy(c_chi).cuda()
+    out_r, out_l = ctx.apply(d_phi, d_chi, occ)
+    torch.cuda.synchronize()
+    r, l = out_r.cpu().numpy(), out_l.cpu().numpy()
+    scale = max(max(np.abs(_ref(g, "out_R", k, S.nbands)).max(), np.abs(_ref(g, "out_L", k, S.nbands)).max())
+                for k in g["sample_k"])
+    for k in g["sample_k"]:
+        er = np.abs(r[k] - _ref(g, "out_R", k, S.nbands)).max() / scale
+        el = np.abs(l[k] - _ref(g, "out_L", k, S.nbands)).max() / scale
+        assert er < tol and el < tol, (k, er, el)
+    E = ctx.energy(d_phi, d_chi, occ)
+    ctx.close()
+    Eref = g["energy"]["total"]
+    nelec = 8.0
+    assert abs(E - Eref) / nelec < etol * max(1.0, abs(Eref)), (E, Eref)
