@@ -184,7 +184,7 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
   if (e == cudaSuccess) ok(cudaMalloc(&c->d_chi, nj * vol));
   if (e == cudaSuccess) ok(cudaMalloc(&c->d_gphi, nj * 3 * vol));
   if (e == cudaSuccess) ok(cudaMalloc(&c->d_gchi, nj * 3 * vol));
-  const size_t side_vols = 25 + (size_t)S.Nk * S.no * 6 + nj * 4;
+  const size_t side_vols = 25 + (size_t)S.Nk * S.no * 9 + nj * 7;   // see fill_side
   c->side_bytes = side_vols * vol;
   if (e == cudaSuccess) ok(cudaMalloc(&c->d_side, 2 * c->side_bytes));
   if (e == cudaSuccess) ok(cudaMemset(c->d_side, 0, 2 * c->side_bytes));

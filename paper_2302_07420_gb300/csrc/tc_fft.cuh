@@ -29,6 +29,17 @@ template <typename T> __device__ __forceinline__ cplx<T> conjg(cplx<T> a) { retu
 template <typename T, int S> __device__ __forceinline__ cplx<T> mul_si(cplx<T> a) {
   return S > 0 ? cplx<T>{-a.y, a.x} : cplx<T>{a.y, -a.x};
 }
+// Read-only (non-coherent) load of a complex value: lets the compiler hoist it
+// above stores to other arrays.
+template <typename T> __device__ __forceinline__ cplx<T> ldg(const cplx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+  } else {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+  }
+}
 // a * conj(b)
 template <typename T> __device__ __forceinline__ cplx<T> mulc(cplx<T> a, cplx<T> b) {
   return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
@@ -226,6 +237,43 @@ __device__ __forceinline__ void inv3d(cplx<T>* W, Load load, Emit emit) {
                         [&](int a, int b, int c, cplx<T> v) { W[G::sidx(a, b, c)] = v; });
   __syncthreads();
   fft_pass<T, N, +1, 1>([&](int a, int b, int c) { return W[G::sidx(a, b, c)]; }, emit);
+}
+
+// Last (axis-1) pass of an inverse transform that feeds a read-modify-write of
+// global arrays.  Per pencil and chunk of CH elements, pre(i1, i2, i3) loads
+// every old value first and post(i1, i2, i3, v, old) then computes and stores,
+// so the loads of a chunk are in flight together instead of one at a time.
+template <typename T, int N, int CH, typename Pre, typename Post>
+__device__ __forceinline__ void inv_axis1_rmw(cplx<T>* W, Pre pre, Post post) {
+  using G = Geo<N>;
+  for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+    const int a = p / N, b = p % N;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = W[G::sidx(i, a, b)];
+    Codelet<T, N, +1>::run(v);
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += CH) {
+      decltype(pre(0, 0, 0)) o[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (c0 + u < N) o[u] = pre(c0 + u, a, b);
+#pragma unroll
+      for (int u = 0; u < CH; ++u)
+        if (c0 + u < N) post(c0 + u, a, b, v[c0 + u], o[u]);
+    }
+  }
+}
+
+template <typename T, int N, int CH, typename Load, typename Pre, typename Post>
+__device__ __forceinline__ void inv3d_rmw(cplx<T>* W, Load load, Pre pre, Post post) {
+  using G = Geo<N>;
+  fft_pass<T, N, +1, 2>(load, [&](int a, int b, int c, cplx<T> v) { W[G::sidx(a, b, c)] = v; });
+  __syncthreads();
+  fft_pass<T, N, +1, 3>([&](int a, int b, int c) { return W[G::sidx(a, b, c)]; },
+                        [&](int a, int b, int c, cplx<T> v) { W[G::sidx(a, b, c)] = v; });
+  __syncthreads();
+  inv_axis1_rmw<T, N, CH>(W, pre, post);
 }
 
 // Pass on a pencil without a transform (pointwise work in the same thread mapping).

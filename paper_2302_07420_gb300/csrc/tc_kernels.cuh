@@ -32,6 +32,8 @@ template <typename T> struct SideArgs {
   cplx<T>* vloc;         // [N]
   cplx<T>* acc;          // [Nk][nb][N]  output accumulator (real space)
   cplx<T>* w;            // [Nk][nb][3][N]
+  cplx<T>* Z;            // [Nk][no][3][N]  -(s2b tw2bx1 grad ket_q + tw3a4 h3a4(q))
+  cplx<T>* Y;            // [Nk][nb][3][N]  tw3b3 h1 ket_j - s2b tw2bx2 grad ket_j
   double* cs;            // [Nk*nb][no][6]: O_qj, X_pp, X_ap (re, im each): 3b6 correction scalars
   const T* tabV;         // [ndelta][2][N] -> this side's V at offset side*N
   T s2b;                 // +1 right, -1 left (sign of the grad u . grad terms)

@@ -251,9 +251,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
       const cplx<T>* bra1 = S.bra + (size_t)q1 * NN;
       const cplx<T>* ket1 = S.ket + (size_t)q1 * NN;
       // A1 = FT[conj(bra_q2) ket_q1], A2 = FT[conj(bra_q1) ket_q2]
-      fwd3d<T, N>(B1, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ket1[g], bra2[g]); },
+      fwd3d<T, N>(B1, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ldg(ket1 + g), ldg(bra2 + g)); },
                   [&](int i, int j, int k, cplx<T> v) { A1[G::sidx(i, j, k)] = P.invN * v; });
-      fwd3d<T, N>(B2, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ket2[g], bra1[g]); },
+      fwd3d<T, N>(B2, [&](int i, int j, int k) { const int g = G::gidx(i, j, k); return mulc(ldg(ket2 + g), ldg(bra1 + g)); },
                   [&](int i, int j, int k, cplx<T> v) { A2[G::sidx(i, j, k)] = P.invN * v; });
       __syncthreads();
       // 3a2 correction pieces for pairs at the same k (Eqs. divcor_3a2_*_density_matrix_mixing)
@@ -283,7 +283,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
                 return mul_si<T, 1>((p[d] * u) * A1[G::sidx(i, j, k)]);
               },
               [&](int i, int j, int k, cplx<T> v) { B1[G::sidx(i, j, k)] = v; });
-          inv3d<T, N>(
+          struct Old3 { cplx<T> h6, a, b; };
+          inv3d_rmw<T, N, 8>(
               B2,
               [&](int i, int j, int k) {
                 T p[3];
@@ -291,14 +292,24 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
                 const T u = P.tabU[((size_t)id12 * 2 + sp) * NN + G::gidx(i, j, k)];
                 return mul_si<T, 1>((p[d] * u) * A2[G::sidx(i, j, k)]);
               },
-              [&](int i, int j, int k, cplx<T> b2) {
+              [&](int i, int j, int k) {
+                const int g = G::gidx(i, j, k);
+                Old3 o;
+                o.h6 = H6[g];
+                if (sp == 0) {
+                  o.a = h3a4[d * NN + g];
+                  o.b = h3b[d * NN + g];
+                }
+                return o;
+              },
+              [&](int i, int j, int k, cplx<T> b2, const Old3& o) {
                 // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
                 const int g = G::gidx(i, j, k);
                 const cplx<T> b1 = B1[G::sidx(i, j, k)];
-                H6[g] = H6[g] + (f1 * f2) * (b1 * b2);
+                H6[g] = o.h6 + (f1 * f2) * (b1 * b2);
                 if (sp == 0) {
-                  h3a4[d * NN + g] = h3a4[d * NN + g] + f1 * (b2 * ket1[g]);
-                  h3b[d * NN + g] = h3b[d * NN + g] + f1 * mulc(b1, bra1[g]);
+                  h3a4[d * NN + g] = o.a + f1 * (b2 * ldg(ket1 + g));
+                  h3b[d * NN + g] = o.b + f1 * mulc(b1, ldg(bra1 + g));
                 }
               });
           __syncthreads();
@@ -367,43 +378,70 @@ template <typename T, int N> __global__ void k_vloc(Params<T> P) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-partner and per-output combinations used by the pair chains (same side):
+//   Z(q)_d = -(s2b tw2bx1 d_d ket_q + tw3a4 h3a4(q)_d)          (q occupied)
+//   Y(j)_d = tw3b3 h1_d ket_j - s2b tw2bx2 d_d ket_j             (every j)
+template <typename T, int N> __global__ void k_prep_zy(Params<T> P) {
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const size_t NN = (size_t)N * N * N;
+  const size_t nz = (size_t)P.Nk * P.no * 3, ny = (size_t)P.Nk * P.nb * 3;
+  const T* tw = P.tw;
+  const T zg = -S.s2b * tw[T2BX1], zh = -tw[T3A4], y1 = tw[T3B3], yg = -S.s2b * tw[T2BX2];
+  const size_t total = (nz + ny) * NN;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t v = e / NN, r = e % NN;
+    if (v < nz) {
+      const size_t qd = v;                       // (k * no + mu) * 3 + d
+      const size_t d = qd % 3, qo = qd / 3;
+      const size_t q = (qo / P.no) * P.nb + qo % P.no;
+      S.Z[e] = zg * S.gket[(q * 3 + d) * NN + r] + zh * S.h3a4[e];
+    } else {
+      const size_t jd = v - nz, d = jd % 3, j = jd / 3;
+      S.Y[jd * NN + r] = y1 * (S.h1[d * NN + r] * S.ket[j * NN + r]) + yg * S.gket[(j * 3 + d) * NN + r];
+    }
+  }
+}
+
 // Fused pair chains, pass 1.  Grid (Nk*nb, 2 sides); CTA = output orbital j.
 // For every occupied partner q (f = f_q / Nk, rho = conj(bra_q) ket_j):
 //   A  = FT[rho]
 //   2ax : acc -= tw f ket_q FT^{-1}[V(Delta + G) A]
 //   for d: b = FT^{-1}[U^pp_d A]
-//        acc -= s2b tw2bx1 f d_d ket_q b + tw3a4 f h3a4(q)_d b;   w_d += f ket_q b
-//        F   = tw3b3 h1_d rho - tw3b5 ket_j h3b(q)_d + tw3b6 n b - s2b tw2bx2 conj(bra_q) d_d ket_j
+//        acc += f Z(q)_d b  (2bx1, 3a4);   w_d += f ket_q b
+//        F   = conj(bra_q) Y(j)_d - tw3b5 ket_j h3b(q)_d + tw3b6 n b   (3b3, 2bx2, 3b5, 3b6 pp)
 //        C  += -U^pp_d FT[F]
 //   for d: b = FT^{-1}[U^ap_d A];  C += -U^ap_d FT[tw3b6 n b]
 //   acc += f ket_q FT^{-1}[C]
 // The inverse transform of b ends on axis 1 and the forward transform of F
 // starts on axis 1, so one thread owns each pencil through the pointwise work.
 // When k_q = k_j the CTA also stores O_qj = A(0) and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G)
-// for the 3b6 corrections.  Slots: 0 B, 1 A, 2 C.
+// for the 3b6 corrections.  Slots: 0 B (work), 1 C (spectral accumulator), 2 A.
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) {
   using G = Geo<N>;
   constexpr int NS = 3;
+  constexpr int CH = 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   __shared__ T red[32];
   const SideArgs<T>& S = P.side[blockIdx.y];
   const int j = blockIdx.x, kj = j / P.nb;
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
-  cplx<T>* A = vol_slot<T, N>(P, sm, 1, NS);
-  cplx<T>* C = vol_slot<T, N>(P, sm, 2, NS);
+  cplx<T>* C = vol_slot<T, N>(P, sm, 1, NS);
+  cplx<T>* A = vol_slot<T, N>(P, sm, 2, NS);
   const size_t NN = G::nn;
   const cplx<T>* ketj = S.ket + (size_t)j * NN;
-  const cplx<T>* gketj = S.gket + (size_t)j * 3 * NN;
+  const cplx<T>* Yj = S.Y + (size_t)j * 3 * NN;
   cplx<T>* acc = S.acc + (size_t)j * NN;
   cplx<T>* w = S.w + (size_t)j * 3 * NN;
   const T* tw = P.tw;
-  const T s2b = S.s2b;
   const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
-  const bool need_pp = need_w || tw[T2BX1] != T(0) || tw[T3A4] != T(0) || tw[T3B6] != T(0);
-  const bool need_F = tw[T3B3] != T(0) || tw[T3B5] != T(0) || tw[T3B6] != T(0) || tw[T2BX2] != T(0);
+  const bool need_z = tw[T2BX1] != T(0) || tw[T3A4] != T(0);
+  const bool need_y = tw[T3B3] != T(0) || tw[T2BX2] != T(0);
+  const bool need_pp = need_w || need_z || tw[T3B6] != T(0);
+  const bool need_F = need_y || tw[T3B5] != T(0) || tw[T3B6] != T(0);
   const bool need_ap = tw[T3B6] != T(0);
+  const T t3b5 = tw[T3B5], t3b6 = tw[T3B6];
   for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
     acc[r] = cplx<T>{0, 0};
     for (int d = 0; d < 3; ++d) w[d * NN + r] = cplx<T>{0, 0};
@@ -421,14 +459,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
       if (f == T(0)) continue;
       const cplx<T>* braq = S.bra + (size_t)q * NN;
       const cplx<T>* ketq = S.ket + (size_t)q * NN;
-      const cplx<T>* gketq = S.gket + (size_t)q * 3 * NN;
-      const cplx<T>* h3a4q = S.h3a4 + ((size_t)(kq * P.no + mu) * 3) * NN;
+      const cplx<T>* Zq = S.Z + ((size_t)(kq * P.no + mu) * 3) * NN;
       const cplx<T>* h3bq = S.h3b + ((size_t)(kq * P.no + mu) * 3) * NN;
       // A = FT[conj(bra_q) ket_j]
-      fwd3d<T, N>(B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ketj[g], braq[g]); },
+      fwd3d<T, N>(B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ketj + g), ldg(braq + g)); },
                   [&](int a, int b, int c, cplx<T> v) { A[G::sidx(a, b, c)] = P.invN * v; });
       __syncthreads();
-      if (P.div && kq == kj && tw[T3B6] != T(0)) {
+      if (P.div && kq == kj && t3b6 != T(0)) {
         // O_qj and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G)
         for (int s = 0; s < 2; ++s) {
           T xr = 0, xi = 0;
@@ -453,11 +490,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
       // 2ax
       if (tw[T2AX] != T(0)) {
         const T fw = -f * tw[T2AX];
-        inv3d<T, N>(B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
-                    [&](int a, int b, int c, cplx<T> v) {
-                      const int g = G::gidx(a, b, c);
-                      acc[g] = acc[g] + fw * (ketq[g] * v);
-                    });
+        inv3d_rmw<T, N, CH>(
+            B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
+            [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
+            [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+              const int g = G::gidx(a, b, c);
+              acc[g] = o + fw * (ldg(ketq + g) * v);
+            });
         __syncthreads();
       }
       // grad-u channels: pp (with the fused second-stage vector field) and ap (3b6)
@@ -486,29 +525,36 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
 #pragma unroll
             for (int i = 0; i < N; ++i) v[i] = B[G::sidx(i, i2, i3)];
             Codelet<T, N, +1>::run(v);
+            if (sp == 0) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-              const int g = G::gidx(i, i2, i3);
-              const cplx<T> bv = v[i];
-              cplx<T> F = {0, 0};
-              if (sp == 0) {
-                const cplx<T> kqv = ketq[g];
-                cplx<T> da = {0, 0};
-                if (tw[T2BX1] != T(0)) da = da + (-s2b * tw[T2BX1] * f) * (gketq[d * NN + g] * bv);
-                if (tw[T3A4] != T(0)) da = da + (-tw[T3A4] * f) * (h3a4q[d * NN + g] * bv);
-                if (tw[T2BX1] != T(0) || tw[T3A4] != T(0)) acc[g] = acc[g] + da;
-                if (need_w) w[d * NN + g] = w[d * NN + g] + f * (kqv * bv);
-                if (need_F) {
-                  const cplx<T> kj_ = ketj[g];
-                  if (tw[T3B3] != T(0)) F = F + tw[T3B3] * (S.h1[d * NN + g] * mulc(kj_, braq[g]));
-                  if (tw[T3B5] != T(0)) F = F - tw[T3B5] * (kj_ * h3bq[d * NN + g]);
-                  if (tw[T3B6] != T(0)) F = F + tw[T3B6] * (S.n[g] * bv);
-                  if (tw[T2BX2] != T(0)) F = F - (s2b * tw[T2BX2]) * mulc(gketj[d * NN + g], braq[g]);
+              for (int c0 = 0; c0 < N; c0 += CH) {
+                cplx<T> oa[CH], ow[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                  if (c0 + u >= N) continue;
+                  const int g = G::gidx(c0 + u, i2, i3);
+                  if (need_z) oa[u] = acc[g];
+                  if (need_w) ow[u] = w[d * NN + g];
                 }
-              } else {
-                F = tw[T3B6] * (S.n[g] * bv);
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                  if (c0 + u >= N) continue;
+                  const int g = G::gidx(c0 + u, i2, i3);
+                  const cplx<T> bv = v[c0 + u];
+                  if (need_z) acc[g] = oa[u] + f * (ldg(Zq + d * NN + g) * bv);
+                  if (need_w) w[d * NN + g] = ow[u] + f * (ldg(ketq + g) * bv);
+                  cplx<T> F = {0, 0};
+                  if (need_F) {
+                    if (need_y) F = mulc(ldg(Yj + d * NN + g), ldg(braq + g));
+                    if (t3b5 != T(0)) F = F - t3b5 * (ldg(ketj + g) * ldg(h3bq + d * NN + g));
+                    if (t3b6 != T(0)) F = F + t3b6 * (ldg(S.n + g) * bv);
+                  }
+                  v[c0 + u] = F;
+                }
               }
-              v[i] = F;
+            } else {
+#pragma unroll
+              for (int i = 0; i < N; ++i) v[i] = t3b6 * (ldg(S.n + G::gidx(i, i2, i3)) * v[i]);
             }
             if (sp == 0 && !need_F) continue;
             Codelet<T, N, -1>::run(v);
@@ -533,11 +579,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
         }
       }
       if (need_F || need_ap) {
-        inv3d<T, N>(B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
-                    [&](int a, int b, int c, cplx<T> v) {
-                      const int g = G::gidx(a, b, c);
-                      acc[g] = acc[g] + f * (ketq[g] * v);
-                    });
+        inv3d_rmw<T, N, CH>(
+            B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
+            [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
+            [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+              const int g = G::gidx(a, b, c);
+              acc[g] = o + f * (ldg(ketq + g) * v);
+            });
         __syncthreads();
       }
     }
@@ -573,7 +621,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
       const cplx<T>* ketq = S.ket + (size_t)q * NN;
       for (int d = 0; d < 3; ++d) {
         fwd3d<T, N>(
-            B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(w[d * NN + g], braq[g]); },
+            B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(w + d * NN + g), ldg(braq + g)); },
             [&](int a, int b, int c, cplx<T> v) {
               T p[3];
               pvec<T, N>(P, dl, a, b, c, p);
@@ -585,11 +633,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
         __syncthreads();
       }
       const T fw = t3b4 * f;
-      inv3d<T, N>(B, [&](int a, int b, int c) { return A[G::sidx(a, b, c)]; },
-                  [&](int a, int b, int c, cplx<T> v) {
-                    const int g = G::gidx(a, b, c);
-                    acc[g] = acc[g] + fw * (ketq[g] * v);
-                  });
+      inv3d_rmw<T, N, 8>(
+          B, [&](int a, int b, int c) { return A[G::sidx(a, b, c)]; },
+          [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
+          [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+            const int g = G::gidx(a, b, c);
+            acc[g] = o + fw * (ldg(ketq + g) * v);
+          });
       __syncthreads();
     }
   }

@@ -12,7 +12,7 @@ constexpr int kSmemLimit = 227 * 1024;   // bytes of shared memory per CTA on sm
 
 template <typename T> static inline size_t side_field_vols(int Nk, int nb, int no) {
   // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc  = 25
-  return 25 + (size_t)Nk * no * 3 * 2 + (size_t)Nk * nb * (1 + 3);
+  return 25 + (size_t)Nk * no * 3 * 3 + (size_t)Nk * nb * (1 + 3 + 3);
 }
 
 template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideArgs<T>& s) {
@@ -28,6 +28,8 @@ template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideAr
   s.h3b = take((size_t)S.Nk * S.no * 3);
   s.acc = take((size_t)S.Nk * S.nb);
   s.w = take((size_t)S.Nk * S.nb * 3);
+  s.Z = take((size_t)S.Nk * S.no * 3);
+  s.Y = take((size_t)S.Nk * S.nb * 3);
   s.cs = ctx->d_cs + (size_t)side * S.Nk * S.nb * S.no * 6;
   const cplx<T>* phi = reinterpret_cast<const cplx<T>*>(ctx->d_phi);
   const cplx<T>* chi = reinterpret_cast<const cplx<T>*>(ctx->d_chi);
@@ -200,7 +202,9 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   }
   k_vloc<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_vloc");
-  nl[2] += 1;
+  k_prep_zy<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
+  TC_CHECK_LAUNCH("k_prep_zy");
+  nl[2] += 2;
   // 4. pair chains
   stage_mark(ctx, st, 3);
   {
