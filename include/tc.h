@@ -29,7 +29,7 @@
  *
  * Ownership: the caller owns every buffer it passes.  The context owns its
  * tables and workspace, all allocated in tc_init; tc_apply / tc_energy
- * allocate nothing.
+ * allocate nothing (tc_apply_noalloc needs no context at all).
  *
  * Errors: no call aborts or throws across the ABI.  On a non-OK status the
  * contents of the output arrays are undefined; tc_last_error gives the reason.
@@ -134,6 +134,51 @@ enum { TC_NSTAGES = 6 };
 tc_status tc_profile(tc_ctx* ctx, int enable);
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
 tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
+
+/* Size of the static device array behind tc_apply_noalloc: 64 MiB per device. */
+#define TC_NOALLOC_MAX_BYTES 67108864
+
+/* tc_apply_noalloc -- tc_apply for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a convenience of this library.
+ *
+ * Who needs it: a host program whose framework has already reserved (almost)
+ * all device memory for its own pool, so a cudaMalloc issued by this library
+ * would fail, or one that forbids allocations from plug-in code during its
+ * run.  Such a caller cannot use tc_init, which allocates the context's
+ * tables and workspace.
+ *
+ * What it does: the same right and left operator as tc_apply (same arrays,
+ * layouts, terms and term_mask), computed by the same kernels, for the
+ * parameters given directly (no context).  Every device buffer of the call
+ * is carved out of one file-scope device array of TC_NOALLOC_MAX_BYTES that
+ * every GPU which has loaded the library holds until the process exits.  The
+ * call makes no cudaMalloc, cudaFree or other allocating library call.  It
+ * rebuilds the host setup (cell, spheres, kernel tables) on every call, so
+ * it spends more host time than tc_apply with a reused context.
+ *
+ * Sizes: a problem whose buffers exceed TC_NOALLOC_MAX_BYTES is rejected with
+ * TC_ERR_UNSUPPORTED before any device work; tc_last_error(NULL) states the
+ * bytes it would need (a 16^3 box with 7 bands at one k-point in FP64 needs
+ * about 30 MB).
+ *
+ * Arguments: phi_R, phi_L, out_R, out_L must be device pointers (host
+ * pointers give TC_ERR_ARG); out_R or out_L may be NULL to skip that side.
+ * occ is a host array [Nk][nbands], read before the call returns.
+ *
+ * First call per device: it looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current) and sets the kernels'
+ * shared-memory attributes and FFT twiddle constants; make this first call on
+ * each device before any stream capture on that device.
+ *
+ * Sharing: all calls on a device use the same array, which keeps the
+ * previous call's contents (each call clears what must start at zero).  Calls
+ * whose GPU work overlaps -- on different streams, or from several threads
+ * without ordering -- race on the array and give undefined results; order
+ * them, e.g. on one stream.
+ *
+ * Errors: as tc_apply; the reason is given by tc_last_error(NULL). */
+tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R, const void* phi_L, const double* occ,
+                           void* out_R, void* out_L, void* cuda_stream);
 
 /* Reason of the last failure on ctx; with ctx == NULL, of the last failed
  * tc_init on the calling thread.  The string lives until the next call. */

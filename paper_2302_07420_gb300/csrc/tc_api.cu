@@ -126,6 +126,11 @@ __global__ void k_energy_dot(const double2* __restrict__ cphi, const double2* __
 
 }  // namespace
 
+namespace tc {
+// Sets the message returned by tc_last_error(NULL) on this thread.
+void set_thread_error(const std::string& msg) { g_init_err = msg; }
+}  // namespace tc
+
 extern "C" {
 
 tc_status tc_init(const tc_params* params, tc_ctx** out) {

@@ -1,0 +1,242 @@
+// tc_apply_noalloc: the operator of tc_apply for callers that cannot allocate
+// device memory (see include/tc.h).  Every device buffer of the call -- the
+// basis maps, the kernel tables, the real-space fields and the pipeline's
+// workspace -- is carved out of one file-scope device array of fixed size, so
+// the call makes no cudaMalloc/cudaFree and no allocating library call.
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "tc_ctx.hpp"
+
+namespace tc {
+void set_thread_error(const std::string& msg);   // defined in tc_api.cu (tc_last_error(NULL))
+}
+
+namespace {
+
+constexpr size_t kNoallocBytes = (size_t)TC_NOALLOC_MAX_BYTES;
+constexpr int kMaxDevices = 64;
+
+// Scratch of every tc_apply_noalloc call on this device.  In host code the
+// name `g_noalloc_arena` is only a host-side stand-in for the symbol: device
+// addresses come from cudaGetSymbolAddress (g_arena_addr below).
+static __device__ __align__(256) unsigned char g_noalloc_arena[kNoallocBytes];
+
+std::mutex g_mu;
+void* g_arena_addr[kMaxDevices] = {};
+unsigned g_prepared[kMaxDevices] = {};   // bit (prec * 8 + size slot): kernel attributes and twiddles set
+
+#define TC_FOR_N(X) X(0, 9) X(1, 12) X(2, 15) X(3, 16) X(4, 24)
+
+template <typename T> int prepare(tc_ctx* c, int n) {
+#define CASE(SLOT, NN) \
+  case NN: return tc::prepare_kernels<T, NN>(c);
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
+template <typename T> size_t scratch_bytes(const tc::Setup& S, int n) {
+#define CASE(SLOT, NN) \
+  case NN: return tc::scratch_needed<T, NN>(S);
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return 0;
+}
+
+template <typename T>
+int run(tc_ctx* c, const double2* a, const double2* b, double2* oR, double2* oL, const double* tw, cudaStream_t st) {
+#define CASE(SLOT, NN) \
+  case NN: return tc::run_pipeline<T, NN>(c, a, b, oR, oL, tw, 2, st);
+  switch (c->S.n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
+int size_slot(int n) {
+#define CASE(SLOT, NN) \
+  case NN: return SLOT;
+  switch (n) { TC_FOR_N(CASE) }
+#undef CASE
+  return -1;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+tc_status fail(tc_status s, const std::string& msg) {
+  tc::set_thread_error("tc_apply_noalloc: " + msg);
+  return s;
+}
+
+// Offsets into the arena (256-byte aligned pieces).
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+struct Layout {
+  size_t box, kpg, did, delta, tabV, tabU, hartV, hartU, hartUs, occ, phi, chi, gphi, gchi, side, cs, scratch, total;
+  size_t side_bytes, scratch_len, cs_bytes;
+};
+
+Layout plan(const tc::Setup& S, size_t esz, size_t rsz, size_t scratch_len) {
+  Layout L{};
+  Carve c;
+  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb, vol = NN * esz;
+  L.box = c.take(S.box_index.size() * sizeof(int));
+  L.kpg = c.take((size_t)S.Nk * S.npw_max * 3 * sizeof(double));
+  L.did = c.take(S.delta_id.size() * sizeof(int));
+  L.delta = c.take((size_t)S.ndelta * 3 * rsz);
+  L.tabV = c.take(S.tabV.size() * rsz);
+  L.tabU = c.take(S.tabU.size() * rsz);
+  L.hartV = c.take(S.hartV.size() * rsz);
+  L.hartU = c.take(S.hartU.size() * rsz);
+  L.hartUs = c.take(S.hartUs.size() * rsz);
+  L.occ = c.take(nj * sizeof(double));
+  L.phi = c.take(nj * vol);
+  L.chi = c.take(nj * vol);
+  L.gphi = c.take(nj * 3 * vol);
+  L.gchi = c.take(nj * 3 * vol);
+  L.side_bytes = (25 + (size_t)S.Nk * S.no * 9 + nj * 7) * vol;   // the per-side field block of tc_init
+  L.side = c.take(2 * L.side_bytes);
+  L.cs_bytes = (size_t)2 * nj * S.no * 6 * sizeof(double);
+  L.cs = c.take(L.cs_bytes);
+  L.scratch_len = scratch_len;
+  L.scratch = c.take(scratch_len);
+  L.total = (c.off + 255) & ~(size_t)255;
+  return L;
+}
+
+// Host FP64 vector -> arena piece in the compute precision (pageable copy on st).
+template <typename T> cudaError_t put(char* dst, const std::vector<double>& v, cudaStream_t st) {
+  if (v.empty()) return cudaSuccess;
+  std::vector<T> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (T)v[i];
+  return cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+}
+
+// Device address of this device's arena (looked up once per device, device current).
+void* arena_address(int dev, cudaError_t& err) {
+  err = cudaSuccess;
+  if (dev < 0 || dev >= kMaxDevices) {
+    err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  if (!g_arena_addr[dev]) {
+    void* p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_noalloc_arena);
+    if (err != cudaSuccess) return nullptr;
+    g_arena_addr[dev] = p;
+  }
+  return g_arena_addr[dev];
+}
+
+}  // namespace
+
+extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R, const void* phi_L,
+                                      const double* occ, void* out_R, void* out_L, void* cuda_stream) {
+  if (!params || !phi_R || !phi_L || !occ) return fail(TC_ERR_ARG, "null argument");
+  if (!out_R && !out_L) return TC_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  tc_ctx c;
+  const std::string why = tc::build_setup(*params, c.S);
+  if (!why.empty()) return fail(why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG, why);
+  const tc::Setup& S = c.S;
+  const size_t nj = (size_t)S.Nk * S.nb;
+  for (size_t i = 0; i < nj; ++i)
+    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return fail(TC_ERR_ARG, "occupations must lie in [0, 1]");
+  c.prec = params->precision;
+  const bool f64 = c.prec == TC_FP64;
+  c.esz = f64 ? 16 : 8;
+  const size_t rsz = f64 ? 8 : 4;
+  const Layout L = plan(S, c.esz, rsz, f64 ? scratch_bytes<double>(S, S.n) : scratch_bytes<float>(S, S.n));
+  if (L.total > kNoallocBytes)
+    return fail(TC_ERR_UNSUPPORTED, "problem needs " + std::to_string(L.total) + " bytes of device scratch; the "
+                                    "static arena holds " + std::to_string(kNoallocBytes) + " (TC_NOALLOC_MAX_BYTES)");
+  for (const void* p : {phi_R, phi_L, (const void*)out_R, (const void*)out_L})
+    if (p && !on_device(p)) return fail(TC_ERR_ARG, "orbital and output arrays must be device pointers");
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  c.device = dev;
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    base = static_cast<char*>(arena_address(dev, e));
+    if (!base) return fail(TC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    const unsigned bit = 1u << ((f64 ? 0 : 8) + size_slot(S.n));
+    if (!(g_prepared[dev] & bit)) {
+      const int r = f64 ? prepare<double>(&c, S.n) : prepare<float>(&c, S.n);
+      if (r != TC_OK) return fail((tc_status)r, c.err);
+      g_prepared[dev] |= bit;
+    }
+  }
+  // basis maps and tables
+  std::vector<double> kpg((size_t)S.Nk * S.npw_max * 3, 0.0);
+  for (int k = 0; k < S.Nk; ++k)
+    for (int g = 0; g < S.npw[k]; ++g)
+      for (int d = 0; d < 3; ++d) {
+        const auto& m = S.miller[k][g];
+        kpg[((size_t)k * S.npw_max + g) * 3 + d] = S.kcart[k][d] + (m[0] * S.B[0][d] + m[1] * S.B[1][d] + m[2] * S.B[2][d]);
+      }
+  std::vector<double> dl;
+  for (auto& d : S.delta) dl.insert(dl.end(), d.begin(), d.end());
+  auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+  ok(cudaMemcpyAsync(base + L.box, S.box_index.data(), S.box_index.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + L.kpg, kpg.data(), kpg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  ok(cudaMemcpyAsync(base + L.did, S.delta_id.data(), S.delta_id.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  const std::vector<double> occ_copy(occ, occ + nj);   // pageable: consumed before the copy call returns
+  ok(cudaMemcpyAsync(base + L.occ, occ_copy.data(), nj * sizeof(double), cudaMemcpyHostToDevice, st));
+  const std::vector<double>* tabs[] = {&dl, &S.tabV, &S.tabU, &S.hartV, &S.hartU, &S.hartUs};
+  const size_t offs[] = {L.delta, L.tabV, L.tabU, L.hartV, L.hartU, L.hartUs};
+  for (int i = 0; i < 6; ++i) ok(f64 ? put<double>(base + offs[i], *tabs[i], st) : put<float>(base + offs[i], *tabs[i], st));
+  // the arena keeps the previous call's contents: start from the zeroed state of a fresh context
+  ok(cudaMemsetAsync(base + L.side, 0, 2 * L.side_bytes, st));
+  ok(cudaMemsetAsync(base + L.cs, 0, L.cs_bytes, st));
+  if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+
+  c.d_box_index = reinterpret_cast<int*>(base + L.box);
+  c.d_kpg = reinterpret_cast<double*>(base + L.kpg);
+  c.d_delta_id = reinterpret_cast<int*>(base + L.did);
+  c.d_delta = base + L.delta;
+  c.d_tabV = base + L.tabV;
+  c.d_tabU = base + L.tabU;
+  c.d_hartV = base + L.hartV;
+  c.d_hartU = base + L.hartU;
+  c.d_hartUs = base + L.hartUs;
+  c.d_occ = reinterpret_cast<double*>(base + L.occ);
+  c.d_phi = base + L.phi;
+  c.d_chi = base + L.chi;
+  c.d_gphi = base + L.gphi;
+  c.d_gchi = base + L.gchi;
+  c.d_side = base + L.side;
+  c.side_bytes = L.side_bytes;
+  c.d_cs = reinterpret_cast<double*>(base + L.cs);
+  c.d_scratch = base + L.scratch;
+  c.scratch_bytes = L.scratch_len;
+  double tw[TC_NTERMS_OP];
+  const unsigned mask = S.prm.term_mask;
+  for (int t = 0; t < TC_NTERMS_OP; ++t) tw[t] = (mask == 0u || ((mask >> t) & 1u)) ? 1.0 : 0.0;
+  const double2* a = static_cast<const double2*>(phi_R);
+  const double2* b = static_cast<const double2*>(phi_L);
+  double2* oR = static_cast<double2*>(out_R);
+  double2* oL = static_cast<double2*>(out_L);
+  const int r = f64 ? run<double>(&c, a, b, oR, oL, tw, st) : run<float>(&c, a, b, oR, oL, tw, st);
+  if (r != TC_OK) return fail((tc_status)r, c.err);
+  return TC_OK;
+}
