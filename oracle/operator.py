@@ -84,9 +84,11 @@ FOUR_PI = 4.0 * np.pi
 class TCOperator:
     """Right (left=False) or left (left=True) TC operator for fixed orbitals."""
 
-    def __init__(self, S, c_phi, c_chi, occ, left=False, backend=None):
+    def __init__(self, S, c_phi, c_chi, occ, left=False, backend=None, kset=None):
         self.S = S
         self.bk = backend if backend is not None else FFTBackend(S)
+        # Jastrow kernel data (values at S.A, S.C unless a displaced set is given, see gradient.py)
+        self.ks = kset if kset is not None else KN.JastrowKernels(S.A, S.C)
         self.left = bool(left)
         self.s2b = -1.0 if self.left else 1.0
         c_phi = np.asarray(c_phi, dtype=np.complex128)
@@ -113,15 +115,15 @@ class TCOperator:
         p2 = np.einsum("...i,...i->...", p, p)
         zero = p2 == 0.0
         p2s = np.where(zero, 1.0, p2)
-        A, C = S.A, S.C
-        V = KN.V2a(p2s, A[0], C[0], adjoint=self.left)
-        v0 = KN.V2a_jastrow_zero(A[0], C[0])
+        ks = self.ks
+        V = ks.V2a(p2s, 0, adjoint=self.left)
+        v0 = ks.v0(0)
         if S.div_correction:
-            v0 = v0 + FOUR_PI * S.Nk * S.Gamma0
+            v0 = v0 + ks.coulomb_zero(S.Nk, S.Gamma0)
         V = np.where(zero, v0, V) / S.Omega
         U = []
         for s in range(2):
-            u = np.where(zero, 0.0, KN.u_tilde(p2s, A[s], C[s])) / S.Omega
+            u = np.where(zero, 0.0, ks.u(p2s, s)) / S.Omega
             U.append(1j * np.moveaxis(p, -1, 0) * u[None])              # (3, grid)
         out = {"V": V, "U": U}
         self._kcache[key] = out
@@ -133,13 +135,13 @@ class TCOperator:
         g2 = np.einsum("...i,...i->...", G, G)
         zero = g2 == 0.0
         g2s = np.where(zero, 1.0, g2)
-        A, C = S.A, S.C
-        Vh = sum(KN.V2a(g2s, A[s], C[s], adjoint=self.left) for s in range(2))
-        uh = sum(KN.u_tilde(g2s, A[s], C[s]) for s in range(2))
+        ks = self.ks
+        Vh = sum(ks.V2a(g2s, s, adjoint=self.left) for s in range(2))
+        uh = sum(ks.u(g2s, s) for s in range(2))
         Vh = np.where(zero, 0.0, Vh) / S.Omega
         uh = np.where(zero, 0.0, uh) / S.Omega
         Uh = 1j * np.moveaxis(G, -1, 0) * uh[None]
-        us = [np.where(zero, 0.0, KN.u_tilde(g2s, A[s], C[s])) for s in range(2)]  # no 1/Omega
+        us = [np.where(zero, 0.0, ks.u(g2s, s)) for s in range(2)]  # no 1/Omega
         return Vh, Uh, us
 
     # ------------------------------------------------------------------ stages
@@ -228,9 +230,8 @@ class TCOperator:
                 Fa = np.sum((f * O[:, q2])[:, None, None, None] * F[q2, :], axis=0)  # FT[chi_q2^* phi_q1](G) <chi_q1|phi_q2>
                 Fb = np.sum((f * O[q2, :])[:, None, None, None] * F[:, q2], axis=0)  # <chi_q2|phi_q1> FT[chi_q1^* phi_q2](G)
                 for s in range(2):
-                    A, C = S.A[s], S.C[s]
-                    c = (FOUR_PI * A) ** 2 * S.Gamma0 + S.ushort_factor * FOUR_PI * A * KN.u_short(A, C) / Nk
-                    field = bk.const(c * F0) + (FOUR_PI * A / Nk) * bk.iFT(self.us[s] * (Fa + Fb))
+                    c = self.ks.corr(s, S.Gamma0, S.ushort_factor, Nk)
+                    field = bk.const(c * F0) + (FOUR_PI * self.ks.amp(s) / Nk) * bk.iFT(self.us[s] * (Fa + Fb))
                     out = out + (f[q2] / Nk) * field / (Om * Om)
         return out
 
@@ -332,8 +333,8 @@ class TCOperator:
         ntneg = bk.spec_neg(nt)
         out = bk.zeros((S.nbands,))
         for s in range(2):
-            A, C = S.A[s], S.C[s]
-            c = (FOUR_PI * A) ** 2 * S.Gamma0 + S.ushort_factor * FOUR_PI * A * KN.u_short(A, C) / Nk
+            c = self.ks.corr(s, S.Gamma0, S.ushort_factor, Nk)
+            A = self.ks.amp(s)
             vu = bk.iFT(self.us[s] * nt)                                          # sum_{G!=0} u~(G) n~(G) e^{iG.r}
             X = np.sum(self.us[s] * F * ntneg, axis=(-3, -2, -1))               # (no, nb)
             one = bk.const(1.0)[None]
@@ -345,8 +346,8 @@ class TCOperator:
         return out
 
 
-def apply_operator(S, c_phi, c_chi, occ, left=False, kpoints=None, terms=TERMS, backend=None):
-    op = TCOperator(S, c_phi, c_chi, occ, left=left, backend=backend(S) if backend else None)
+def apply_operator(S, c_phi, c_chi, occ, left=False, kpoints=None, terms=TERMS, backend=None, kset=None):
+    op = TCOperator(S, c_phi, c_chi, occ, left=left, backend=backend(S) if backend else None, kset=kset)
     return op.apply(kpoints=kpoints, terms=terms)
 
 
@@ -371,13 +372,13 @@ def kinetic_coeffs(S, c):
     return out
 
 
-def energy_terms(S, c_phi, c_chi, occ, res=None, backend=None):
+def energy_terms(S, c_phi, c_chi, occ, res=None, backend=None, kset=None):
     """Per-term pseudo-energies per unit cell (both spins) and their total."""
     c_phi = np.asarray(c_phi, dtype=np.complex128)
     c_chi = np.asarray(c_chi, dtype=np.complex128)
     occ = np.asarray(occ, dtype=np.float64).reshape(S.Nk, S.nbands)
     if res is None:
-        res = apply_operator(S, c_phi, c_chi, occ, left=False, backend=backend)
+        res = apply_operator(S, c_phi, c_chi, occ, left=False, backend=backend, kset=kset)
     pref = 2.0 / S.Nk
     E = {}
     tk = kinetic_coeffs(S, c_phi)
