@@ -117,6 +117,28 @@ tc_status tc_apply(tc_ctx* ctx, const void* phi_R, const void* phi_L, const doub
 tc_status tc_energy(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ,
                     double* E_total, double* E_terms, void* cuda_stream);
 
+/* Gradient of the energy of tc_energy (Eqs. EtotTC / EtotBiTC in the
+ * single-determinant form given there).
+ * Convention for the orbital gradients: g = dE/dRe(c) + i dE/dIm(c), so that
+ * dE = Re sum conj(g) dc (PyTorch's convention for real functions of complex
+ * tensors).  Layout as the orbitals.
+ *   dE_dphiR  gradient with respect to the right orbitals phi  = (2/Nk) f (T chi + h^dagger chi)
+ *   dE_dphiL  gradient with respect to the left orbitals chi   = (2/Nk) f (T phi + h phi)
+ * i.e. the left and right operator outputs plus the kinetic term; this holds
+ * with the SCF-mesh divergence corrections included.
+ *   dE_dA[s], dE_dC[s]  partial derivatives with respect to A_s, C_s
+ *   (s = 0 parallel, 1 antiparallel spins) at fixed orbitals.  E is a
+ *   polynomial of degree 2 in the kernel data (Jastrow tables and correction
+ *   coefficients), so each is the exact symmetric difference of two energy
+ *   evaluations with the kernel data displaced along its derivative; the
+ *   pair densities are recomputed in each evaluation.
+ * Any output may be NULL (skipped).  Requires occ = 0 for bands >= nocc
+ * (TC_ERR_ARG) and, for the orbital gradients, term_mask = 0
+ * (TC_ERR_UNSUPPORTED).  Orbital outputs may be host or device pointers.
+ * Blocks the host until the results are complete. */
+tc_status tc_energy_grad(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, void* dE_dphiR,
+                         void* dE_dphiL, double dE_dA[2], double dE_dC[2], void* cuda_stream);
+
 /* Batched 3D FFT of `batch` contiguous n^3 complex volumes in place on the
  * device (precision TC_FP64: complex128, TC_FP32: complex64), sign -1
  * (sum f e^{-2 pi i m.r/n}) or +1; unnormalised.  Exposes the library's

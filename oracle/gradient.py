@@ -13,8 +13,8 @@ convention of PyTorch for real-valued functions of complex tensors).
 
 Orbitals.  E depends on the ket coefficients phi and on the conjugated bra
 coefficients chi^*.  The two- and three-body operators are the derivatives of
-the two- and three-body parts of E (the SCF equations of Sec. 2.1 make the
-energy stationary; the identity is pinned exactly below), so
+the two- and three-body parts of E (an identity of the single-determinant
+energy, pinned exactly below), so
     g_chi = (2/N_k) f (T phi + h phi)        (right operator output),
     g_phi = (2/N_k) f (T chi + h^dagger chi) (left operator output).
 With the SCF-mesh divergence corrections included this still holds: the 2ax

@@ -1,4 +1,5 @@
 // C ABI of the TC operator library (see include/tc.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -122,6 +123,42 @@ __global__ void k_energy_dot(const double2* __restrict__ cphi, const double2* __
     for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) { ax += rx[i]; ay += ry[i]; }
     e[j] = make_double2(ax, ay);
   }
+}
+
+// Orbital gradient of E (dE = Re sum conj(g) dc):
+//   g_phi = pref f (T chi + out_L),  g_chi = pref f (T phi + out_R),  T = |k+G|^2/2, pref = 2/Nk.
+// g_phi may alias out_L and g_chi may alias out_R (each element is read before it is written).
+__global__ void k_grad_combine(const double2* __restrict__ cphi, const double2* __restrict__ cchi, const double2* outR,
+                               const double2* outL, const double* __restrict__ kpg, const double* __restrict__ occ,
+                               int npw_max, int nb, double pref, size_t total, double2* gphi, double2* gchi) {
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = e / npw_max, g = e % npw_max, k = j / nb;
+    const double* q = kpg + (k * npw_max + g) * 3;
+    const double t = 0.5 * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    const double w = pref * occ[j];
+    if (gphi) {
+      const double2 x = cchi[e], o = outL[e];
+      gphi[e] = make_double2(w * (t * x.x + o.x), w * (t * x.y + o.y));
+    }
+    if (gchi) {
+      const double2 x = cphi[e], o = outR[e];
+      gchi[e] = make_double2(w * (t * x.x + o.x), w * (t * x.y + o.y));
+    }
+  }
+}
+
+// Uploads host FP64 kernel data into the context's device tables (compute precision).
+template <typename T> cudaError_t put_tables(tc_ctx* c, const tc::KernelData& kd, cudaStream_t st) {
+  const std::vector<double>* src[] = {&kd.tabV, &kd.tabU, &kd.hartV, &kd.hartU, &kd.hartUs};
+  void* dst[] = {c->d_tabV, c->d_tabU, c->d_hartV, c->d_hartU, c->d_hartUs};
+  for (int i = 0; i < 5; ++i) {
+    std::vector<T> h(src[i]->size());
+    for (size_t e = 0; e < h.size(); ++e) h[e] = (T)(*src[i])[e];
+    // pageable source: the call returns once the data is staged, so h may go out of scope
+    const cudaError_t r = cudaMemcpyAsync(dst[i], h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (r != cudaSuccess) return r;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -283,6 +320,24 @@ static tc_status run_common(tc_ctx* c, const void* phi, const void* chi, const d
   return TC_OK;
 }
 
+// (2/Nk) Re sum_j f_j <chi_j| (kin ? T phi_j : 0) + (with_out ? out_R_j : 0) > in FP64; blocks the host.
+static tc_status energy_reduce(tc_ctx* c, const double2* dphi, const double2* dchi, const double* occ, bool kin,
+                               bool with_out, cudaStream_t st, double* res) {
+  const tc::Setup& S = c->S;
+  const int nj = S.Nk * S.nb;
+  k_energy_dot<<<nj, 128, 0, st>>>(dphi, dchi, with_out ? c->d_out_R : nullptr, c->d_kpg, S.npw_max, S.nb, kin ? 1 : 0,
+                                   c->d_edot);
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "k_energy_dot");
+  e2 = cudaMemcpyAsync(c->h_edot, c->d_edot, nj * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "energy reduction");
+  double s = 0.0;
+  for (int j = 0; j < nj; ++j) s += occ[j] * c->h_edot[j].x;
+  *res = 2.0 / S.Nk * s;
+  return TC_OK;
+}
+
 static void term_weights(const tc_ctx* c, double* tw, double two, double three) {
   const unsigned mask = c->S.prm.term_mask;
   for (int t = 0; t < NT; ++t) {
@@ -330,17 +385,7 @@ tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* o
     dchi = c->d_in_chi;
   }
   auto reduce = [&](bool kin, bool with_out, double* res) -> tc_status {
-    k_energy_dot<<<nj, 128, 0, st>>>(dphi, dchi, with_out ? c->d_out_R : nullptr, c->d_kpg, S.npw_max, S.nb, kin ? 1 : 0,
-                                     c->d_edot);
-    cudaError_t e2 = cudaGetLastError();
-    if (e2 != cudaSuccess) return cuda_fail(c, e2, "k_energy_dot");
-    e2 = cudaMemcpyAsync(c->h_edot, c->d_edot, nj * sizeof(double2), cudaMemcpyDeviceToHost, st);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
-    if (e2 != cudaSuccess) return cuda_fail(c, e2, "energy reduction");
-    double s = 0.0;
-    for (int j = 0; j < nj; ++j) s += occ[j] * c->h_edot[j].x;
-    *res = 2.0 / S.Nk * s;
-    return TC_OK;
+    return energy_reduce(c, dphi, dchi, occ, kin, with_out, st, res);
   };
   double tw[NT];
   bool host_out = false;
@@ -360,6 +405,113 @@ tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* o
     }
     if ((r = reduce(true, false, &E_terms[TC_TERM_KIN])) != TC_OK) return r;
   }
+  return TC_OK;
+}
+
+tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const double* occ, void* dE_dphiR,
+                         void* dE_dphiL, double* dE_dA, double* dE_dC, void* stream) {
+  if (!c) return TC_ERR_STATE;
+  if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tc::Setup& S = c->S;
+  const int nj = S.Nk * S.nb;
+  for (int k = 0; k < S.Nk; ++k)
+    for (int mu = S.no; mu < S.nb; ++mu)
+      if (occ[k * S.nb + mu] != 0.0)
+        return fail(c, TC_ERR_ARG, "tc_energy_grad needs occ = 0 for bands >= nocc (the partners carry the energy)");
+  const bool want_orb = dE_dphiR || dE_dphiL;
+  if (want_orb && S.prm.term_mask != 0u)
+    return fail(c, TC_ERR_UNSUPPORTED, "the orbital gradient is the operator only with every term on (term_mask 0)");
+  const size_t orb = (size_t)nj * S.npw_max * sizeof(double2);
+  const double2* dphi = static_cast<const double2*>(phi);
+  const double2* dchi = static_cast<const double2*>(chi);
+  cudaError_t e;
+  if (!is_device_ptr(phi)) {
+    if ((e = cudaMemcpyAsync(c->d_in_phi, phi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    dphi = c->d_in_phi;
+  }
+  if (!is_device_ptr(chi)) {
+    if ((e = cudaMemcpyAsync(c->d_in_chi, chi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+    dchi = c->d_in_chi;
+  }
+  bool host_out = false;
+  tc_status r;
+  // 1. orbitals: both operator outputs, then g = (2/Nk) f (T x + out)
+  if (want_orb) {
+    double tw[NT];
+    term_weights(c, tw, 1.0, 1.0);
+    if ((r = run_common(c, dphi, dchi, occ, c->d_out_R, c->d_out_L, tw, 2, st, &host_out)) != TC_OK) return r;
+    double2* gphi = dE_dphiR ? (is_device_ptr(dE_dphiR) ? static_cast<double2*>(dE_dphiR) : c->d_out_L) : nullptr;
+    double2* gchi = dE_dphiL ? (is_device_ptr(dE_dphiL) ? static_cast<double2*>(dE_dphiL) : c->d_out_R) : nullptr;
+    const size_t total = (size_t)nj * S.npw_max;
+    k_grad_combine<<<2 * 152, 256, 0, st>>>(dphi, dchi, c->d_out_R, c->d_out_L, c->d_kpg, c->d_occ, S.npw_max, S.nb,
+                                            2.0 / S.Nk, total, gphi, gchi);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "k_grad_combine");
+    if (dE_dphiR && gphi == c->d_out_L &&
+        (e = cudaMemcpyAsync(dE_dphiR, gphi, orb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(c, e, "dE_dphiR download");
+    if (dE_dphiL && gchi == c->d_out_R &&
+        (e = cudaMemcpyAsync(dE_dphiL, gchi, orb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return cuda_fail(c, e, "dE_dphiL download");
+  }
+  // 2. Jastrow parameters: E is quadratic in the kernel data K, so along dK = dK/dtheta the
+  //    symmetric difference [E(K + t dK) - E(K - t dK)] / 2t is exact for any t.
+  if (dE_dA || dE_dC) {
+    if (c->dkd.empty()) {
+      try {
+        c->dkd.resize(4);
+        for (int m = 0; m < 4; ++m) tc::kernel_data(S, m, c->dkd[m]);
+      } catch (const std::bad_alloc&) {
+        c->dkd.clear();
+        return fail(c, TC_ERR_OOM, "derivative tables: host allocation failed");
+      }
+    }
+    const double corr0[2] = {S.corr_c[0], S.corr_c[1]}, amp0[2] = {S.amp[0], S.amp[1]};
+    tc::KernelData base;
+    base.tabV = S.tabV; base.tabU = S.tabU; base.hartV = S.hartV; base.hartU = S.hartU; base.hartUs = S.hartUs;
+    double twE[NT];
+    term_weights(c, twE, 0.5, 1.0 / 3.0);
+    r = TC_OK;
+    for (int m = 0; m < 4 && r == TC_OK; ++m) {
+      double* dst = m < 2 ? dE_dA : dE_dC;
+      if (!dst) continue;
+      const double theta = m < 2 ? S.prm.A[m] : S.prm.C[m - 2];
+      const double t = 0.5 * std::max(std::fabs(theta), 0.1);
+      const tc::KernelData& dk = c->dkd[m];
+      double Epm[2] = {0.0, 0.0};
+      for (int sg = 0; sg < 2 && r == TC_OK; ++sg) {
+        const double a = sg == 0 ? t : -t;
+        tc::KernelData kd;
+        auto axpy = [&](const std::vector<double>& x, const std::vector<double>& dx, std::vector<double>& y) {
+          y.resize(x.size());
+          for (size_t i = 0; i < x.size(); ++i) y[i] = x[i] + a * dx[i];
+        };
+        axpy(base.tabV, dk.tabV, kd.tabV);
+        axpy(base.tabU, dk.tabU, kd.tabU);
+        axpy(base.hartV, dk.hartV, kd.hartV);
+        axpy(base.hartU, dk.hartU, kd.hartU);
+        axpy(base.hartUs, dk.hartUs, kd.hartUs);
+        e = c->prec == TC_FP64 ? put_tables<double>(c, kd, st) : put_tables<float>(c, kd, st);
+        if (e != cudaSuccess) { r = cuda_fail(c, e, "displaced tables"); break; }
+        for (int s = 0; s < 2; ++s) {
+          S.corr_c[s] = corr0[s] + a * dk.corr_c[s];
+          S.amp[s] = amp0[s] + a * dk.amp[s];
+        }
+        r = run_common(c, dphi, dchi, occ, c->d_out_R, nullptr, twE, 1, st, &host_out);
+        if (r == TC_OK) r = energy_reduce(c, dphi, dchi, occ, false, true, st, &Epm[sg]);
+      }
+      if (r == TC_OK) dst[m % 2] = (Epm[0] - Epm[1]) / (2.0 * t);
+    }
+    // restore the kernel data of the context (also after a failure)
+    for (int s = 0; s < 2; ++s) {
+      S.corr_c[s] = corr0[s];
+      S.amp[s] = amp0[s];
+    }
+    e = c->prec == TC_FP64 ? put_tables<double>(c, base, st) : put_tables<float>(c, base, st);
+    if (r != TC_OK) return r;
+    if (e != cudaSuccess) return cuda_fail(c, e, "table restore");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "tc_energy_grad");
   return TC_OK;
 }
 

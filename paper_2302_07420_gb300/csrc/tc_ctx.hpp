@@ -37,6 +37,8 @@ struct tc_ctx {
   double2* d_edot = nullptr;       // [Nk*nb]
   double2* h_edot = nullptr;       // pinned
   std::vector<int> npw_host;
+  // derivative kernel data d/dA_pp, d/dA_ap, d/dC_pp, d/dC_ap (host, FP64), built by the first tc_energy_grad
+  std::vector<tc::KernelData> dkd;
   // profiling (tc_profile / tc_stage_times)
   bool profile = false;
   cudaEvent_t ev[8] = {};

@@ -53,7 +53,7 @@ template <typename T, int N> static Params<T> make_params(tc_ctx* ctx, const dou
   P.invN = (T)(1.0 / ((double)N * N * N));
   P.Omega = S.Omega;
   P.invOm2 = 1.0 / (S.Omega * S.Omega);
-  for (int s = 0; s < 2; ++s) { P.corr_c[s] = S.corr_c[s]; P.A[s] = S.prm.A[s]; }
+  for (int s = 0; s < 2; ++s) { P.corr_c[s] = S.corr_c[s]; P.A[s] = S.amp[s]; }
   for (int t = 0; t < NT; ++t) P.tw[t] = (T)tw[t];
   P.delta_id = ctx->d_delta_id;
   P.delta = reinterpret_cast<const T*>(ctx->d_delta);

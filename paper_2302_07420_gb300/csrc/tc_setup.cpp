@@ -55,10 +55,93 @@ double host_gradu_sq(double p, double A, double C) {
   return k4Pi * A * A / (C * g) * B_of_g(g);
 }
 
-static double V2a(double p2, double A, double C, bool dagger) {
-  const double lap = lap_u(p2, A, C);
-  return k4Pi / p2 + (dagger ? -lap : lap) - host_gradu_sq(std::sqrt(p2), A, C);
+// D(g) = g B'(g) - 2 B(g), with B'(g) = 2/(4 + g^2) + g (2 atan g - atan(g/2) - pi/2);
+// the same three branches as B_of_g (for g > 1 the bracket is atan(2/g) - 2 atan(1/g),
+// for g > 6 the series gives D = -sum_k (2k + 3) c_k g^-(2k+1)).
+static double D_of_g(double g) {
+  if (g <= 1.0) {
+    const double dB = 2.0 / (4.0 + g * g) + g * (2.0 * std::atan(g) - std::atan(0.5 * g) - 0.5 * kPi);
+    return g * dB - 2.0 * B_of_g(g);
+  }
+  if (g <= 6.0) {
+    const double dB = 2.0 / (4.0 + g * g) + g * (std::atan(2.0 / g) - 2.0 * std::atan(1.0 / g));
+    return g * dB - 2.0 * B_of_g(g);
+  }
+  const double inv2 = 1.0 / (g * g);
+  double pw = inv2 / g;
+  double sum = 0.0;
+  double p2k1 = 8.0;
+  for (int k = 1; k < 60; ++k) {
+    const double ck = ((k & 1) ? -1.0 : 1.0) * ((p2k1 - 1.0) / (2 * k + 1) - (2.0 * p2k1 - 1.0) / (2 * k + 3));
+    const double t = -(2 * k + 3) * ck * pw;
+    sum += t;
+    pw *= inv2;
+    p2k1 *= 4.0;
+    if (std::fabs(t) < 1e-30 * std::fabs(sum)) break;
+  }
+  return sum;
 }
+
+// One Jastrow channel (A, C) and what to evaluate: the kernel (wrt = -1), its
+// derivative with respect to A (wrt = 0) or C (wrt = 1), or nothing (wrt = 2,
+// a channel the derivative does not touch).
+struct Chan {
+  double A, C;
+  int wrt;
+};
+
+static double ch_u(double p2, const Chan& c) {   // u~(p), p > 0
+  const double c2 = 1.0 / (c.C * c.C);
+  switch (c.wrt) {
+    case -1: return host_u_tilde(p2, c.A, c.C);
+    case 0: return k4Pi * c2 / (p2 * (p2 + c2));
+    case 1: return -2.0 * k4Pi * c.A / (c.C * c.C * c.C * (p2 + c2) * (p2 + c2));
+    default: return 0.0;
+  }
+}
+
+static double ch_lap(double p2, const Chan& c) {   // (lap u)~(p)
+  const double c2 = 1.0 / (c.C * c.C);
+  switch (c.wrt) {
+    case -1: return lap_u(p2, c.A, c.C);
+    case 0: return -k4Pi * c2 / (p2 + c2);
+    case 1: return 2.0 * k4Pi * c.A * p2 / (c.C * c.C * c.C * (p2 + c2) * (p2 + c2));
+    default: return 0.0;
+  }
+}
+
+static double ch_gsq(double p, const Chan& c) {   // ((grad u)^2)~(p), p >= 0
+  const double g = c.C * p;
+  switch (c.wrt) {
+    case -1: return host_gradu_sq(p, c.A, c.C);
+    case 0: return g == 0.0 ? k4Pi * c.A / c.C : 2.0 * k4Pi * c.A / (c.C * g) * B_of_g(g);
+    case 1: return g == 0.0 ? -2.0 * kPi * c.A * c.A / (c.C * c.C) : k4Pi * c.A * c.A / (c.C * c.C * c.C * p) * D_of_g(g);
+    default: return 0.0;
+  }
+}
+
+// finite Jastrow part of V_2a at p = 0: (lap u)~(0) - ((grad u)^2)~(0) = -4 pi A - 2 pi A^2 / C
+static double ch_v0(const Chan& c) {
+  switch (c.wrt) {
+    case -1: return -k4Pi * c.A - 2.0 * kPi * c.A * c.A / c.C;
+    case 0: return -k4Pi - k4Pi * c.A / c.C;
+    case 1: return 2.0 * kPi * c.A * c.A / (c.C * c.C);
+    default: return 0.0;
+  }
+}
+
+// (4 pi A)^2 Gamma0 + x 4 pi A u_short / Nk with u_short = -4 pi A C^2 (Eq. u_short)
+static double ch_corr(const Chan& c, double Gamma0, double x, int Nk) {
+  const double a2 = k4Pi * c.A * k4Pi * c.A;
+  switch (c.wrt) {
+    case -1: return a2 * (Gamma0 - x * c.C * c.C / Nk);
+    case 0: return 2.0 * k4Pi * k4Pi * c.A * (Gamma0 - x * c.C * c.C / Nk);
+    case 1: return a2 * (-2.0 * x * c.C / Nk);
+    default: return 0.0;
+  }
+}
+
+static double ch_amp(const Chan& c) { return c.wrt == -1 ? c.A : (c.wrt == 0 ? 1.0 : 0.0); }
 
 // --- small linear algebra ----------------------------------------------------
 static double det3(const double M[3][3]) {
@@ -197,10 +280,6 @@ std::string build_setup(const tc_params& p, Setup& S) {
     S.alpha = (best / 12.0) * (best / 12.0);
   }
   S.Gamma0 = S.Omega / (4.0 * std::sqrt(kPi * kPi * kPi * S.alpha)) - (-S.alpha + aux_sum(S, S.alpha)) / S.Nk;
-  for (int s = 0; s < 2; ++s) {
-    const double A = p.A[s], C = p.C[s];
-    S.corr_c[s] = (k4Pi * A) * (k4Pi * A) * S.Gamma0 + p.ushort_factor * k4Pi * A * (-k4Pi * A * C * C) / S.Nk;
-  }
 
   // distinct Delta = k_out - k_part
   std::map<std::tuple<long, long, long>, int> ids;
@@ -226,12 +305,39 @@ std::string build_setup(const tc_params& p, Setup& S) {
     }
   S.ndelta = (int)S.delta.size();
 
-  // tables
+  KernelData kd;
+  kernel_data(S, KD_VALUE, kd);
+  S.tabV = std::move(kd.tabV);
+  S.tabU = std::move(kd.tabU);
+  S.hartV = std::move(kd.hartV);
+  S.hartU = std::move(kd.hartU);
+  S.hartUs = std::move(kd.hartUs);
+  for (int s = 0; s < 2; ++s) {
+    S.corr_c[s] = kd.corr_c[s];
+    S.amp[s] = kd.amp[s];
+  }
+  return "";
+}
+
+void kernel_data(const Setup& S, int mode, KernelData& kd) {
+  const tc_params& p = S.prm;
+  const int n = S.n;
   const size_t N = S.N;
-  S.tabV.assign((size_t)S.ndelta * 2 * N, 0.0);
-  S.tabU.assign((size_t)S.ndelta * 2 * N, 0.0);
-  const double vj0 = -k4Pi * p.A[0] - 2.0 * kPi * p.A[0] * p.A[0] / p.C[0];   // finite Jastrow part at p = 0
-  const double v0 = (vj0 + (p.div_correction ? k4Pi * S.Nk * S.Gamma0 : 0.0)) / S.Omega;
+  const bool value = mode == KD_VALUE;
+  Chan ch[2];
+  for (int s = 0; s < 2; ++s) {
+    ch[s] = {p.A[s], p.C[s], -1};
+    if (!value) ch[s].wrt = (mode % 2 == s) ? mode / 2 : 2;
+  }
+  const double coul = value ? 1.0 : 0.0;   // the Coulomb part does not depend on A or C
+  for (int s = 0; s < 2; ++s) {
+    kd.corr_c[s] = ch_corr(ch[s], S.Gamma0, p.ushort_factor, S.Nk);
+    kd.amp[s] = ch_amp(ch[s]);
+  }
+  // exchange tables at p = Delta + G; V uses the parallel-spin channel
+  kd.tabV.assign((size_t)S.ndelta * 2 * N, 0.0);
+  kd.tabU.assign((size_t)S.ndelta * 2 * N, 0.0);
+  const double v0 = (ch_v0(ch[0]) + (value && p.div_correction ? k4Pi * S.Nk * S.Gamma0 : 0.0)) / S.Omega;
   for (int id = 0; id < S.ndelta; ++id)
     for (int i1 = 0; i1 < n; ++i1)
       for (int i2 = 0; i2 < n; ++i2)
@@ -241,23 +347,25 @@ std::string build_setup(const tc_params& p, Setup& S) {
           for (int d = 0; d < 3; ++d) pv[d] = S.delta[id][d] + (r1 * S.B[0][d] + r2 * S.B[1][d] + r3 * S.B[2][d]);
           const double p2 = pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2];
           const size_t g = ((size_t)i1 * n + i2) * n + i3;
-          double* V = &S.tabV[(size_t)id * 2 * N];
-          double* U = &S.tabU[(size_t)id * 2 * N];
+          double* V = &kd.tabV[(size_t)id * 2 * N];
+          double* U = &kd.tabU[(size_t)id * 2 * N];
           if (p2 == 0.0) {
             V[g] = v0;
             V[N + g] = v0;   // the adjoint of the discrete right operator keeps V_2a(0)
             U[g] = 0.0;
             U[N + g] = 0.0;
           } else {
-            V[g] = V2a(p2, p.A[0], p.C[0], false) / S.Omega;
-            V[N + g] = V2a(p2, p.A[0], p.C[0], true) / S.Omega;
-            U[g] = host_u_tilde(p2, p.A[0], p.C[0]) / S.Omega;
-            U[N + g] = host_u_tilde(p2, p.A[1], p.C[1]) / S.Omega;
+            const double lap = ch_lap(p2, ch[0]), gsq = ch_gsq(std::sqrt(p2), ch[0]);
+            V[g] = (coul * k4Pi / p2 + lap - gsq) / S.Omega;
+            V[N + g] = (coul * k4Pi / p2 - lap - gsq) / S.Omega;
+            U[g] = ch_u(p2, ch[0]) / S.Omega;
+            U[N + g] = ch_u(p2, ch[1]) / S.Omega;
           }
         }
-  S.hartV.assign(2 * N, 0.0);
-  S.hartU.assign(N, 0.0);
-  S.hartUs.assign(2 * N, 0.0);
+  // Hartree-type tables at G (G = 0 dropped), both channels summed
+  kd.hartV.assign(2 * N, 0.0);
+  kd.hartU.assign(N, 0.0);
+  kd.hartUs.assign(2 * N, 0.0);
   for (int i1 = 0; i1 < n; ++i1)
     for (int i2 = 0; i2 < n; ++i2)
       for (int i3 = 0; i3 < n; ++i3) {
@@ -269,17 +377,17 @@ std::string build_setup(const tc_params& p, Setup& S) {
         const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
         double vr = 0, vl = 0, u = 0;
         for (int s = 0; s < 2; ++s) {
-          vr += V2a(g2, p.A[s], p.C[s], false);
-          vl += V2a(g2, p.A[s], p.C[s], true);
-          const double us = host_u_tilde(g2, p.A[s], p.C[s]);
+          const double lap = ch_lap(g2, ch[s]), gsq = ch_gsq(std::sqrt(g2), ch[s]);
+          vr += coul * k4Pi / g2 + lap - gsq;
+          vl += coul * k4Pi / g2 - lap - gsq;
+          const double us = ch_u(g2, ch[s]);
           u += us;
-          S.hartUs[(size_t)s * N + g] = us;
+          kd.hartUs[(size_t)s * N + g] = us;
         }
-        S.hartV[g] = vr / S.Omega;
-        S.hartV[N + g] = vl / S.Omega;
-        S.hartU[g] = u / S.Omega;
+        kd.hartV[g] = vr / S.Omega;
+        kd.hartV[N + g] = vl / S.Omega;
+        kd.hartU[g] = u / S.Omega;
       }
-  return "";
 }
 
 }  // namespace tc

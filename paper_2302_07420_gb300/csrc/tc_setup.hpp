@@ -33,7 +33,19 @@ struct Setup {
   std::vector<double> hartU;   // [N]             (u~pp + u~ap)(G), 0 at G = 0
   std::vector<double> hartUs;  // [2][N]          u~_s(G) (NOT divided by Omega), 0 at G = 0
   double corr_c[2]{};          // (4 pi A_s)^2 Gamma0 + x 4 pi A_s u_short,s / Nk
+  double amp[2]{};             // A_s as used by the corrections (4 pi A_s / Nk)
 };
+
+// The Jastrow-dependent kernel data: the tables of Setup and the correction
+// scalars.  mode -1: values at (A, C); mode 0..3: their derivatives with
+// respect to A_pp, A_ap, C_pp, C_ap (zero for the other channel and for the
+// Coulomb part).
+struct KernelData {
+  std::vector<double> tabV, tabU, hartV, hartU, hartUs;
+  double corr_c[2]{}, amp[2]{};
+};
+enum { KD_VALUE = -1, KD_DA_PP = 0, KD_DA_AP = 1, KD_DC_PP = 2, KD_DC_AP = 3 };
+void kernel_data(const Setup& S, int mode, KernelData& kd);
 
 // Returns an empty string on success, otherwise the reason.
 std::string build_setup(const tc_params& p, Setup& S);

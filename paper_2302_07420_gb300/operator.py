@@ -109,6 +109,27 @@ class Context:
         d["kin"] = Et[16]
         return E.value, d
 
+    def energy_grad(self, phi_R, phi_L, occ, orbitals=True, params=True, stream=None):
+        """Gradient of energy(): (g_phi, g_chi, dE_dA[2], dE_dC[2]).
+
+        g = dE/dRe(c) + i dE/dIm(c) for the right (phi) and left (chi) coefficients
+        (torch complex128 on the orbitals' device); dE_dA, dE_dC are numpy arrays
+        [parallel, antiparallel].  Skipped parts are returned as None.
+        """
+        import torch
+        phi_R = self._check_orbitals(phi_R).contiguous()
+        phi_L = self._check_orbitals(phi_L).contiguous()
+        occ_np, occ_p = self._occ(occ)
+        g_phi = torch.empty_like(phi_R) if orbitals else None
+        g_chi = torch.empty_like(phi_L) if orbitals else None
+        dA = (ctypes.c_double * 2)() if params else None
+        dC = (ctypes.c_double * 2)() if params else None
+        st = self.lib.tc_energy_grad(self.h, _ptr(phi_R), _ptr(phi_L), occ_p,
+                                     _ptr(g_phi) if orbitals else None, _ptr(g_chi) if orbitals else None,
+                                     dA, dC, _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return (g_phi, g_chi, np.array(dA[:]) if params else None, np.array(dC[:]) if params else None)
+
     def profile(self, enable=True):
         """Enable (and reset) or disable per-stage device timing."""
         _lib.check(self.lib, self.h, self.lib.tc_profile(self.h, 1 if enable else 0))

@@ -6,7 +6,12 @@ Stored: out_R / out_L (every term summed) at the sampled k-points, E_TC and its
 per-term split, and a few input coefficients to confirm that the regenerated
 inputs are the ones used here.
 
+si_k222_grad: the same cell, box and recipe on a 2x2x2 mesh (seed 230207420 + 5):
+the energy gradient of oracle/gradient.py -- g_phi, g_chi at the sampled
+k-points and dE/dA, dE/dC -- and E_TC.
+
 Run:  python tests/golden/make_golden.py si_k444
+      python tests/golden/make_golden.py si_k222_grad
 """
 import json
 import os
@@ -18,17 +23,18 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from oracle import gradient as GR  # noqa: E402
 from oracle import operator as OP  # noqa: E402
 from oracle.cell import Setup  # noqa: E402
 from paper_2302_07420_gb300 import synth  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SAMPLE_K = {"si_k444": [0, 21, 42]}
-SEED_OFFSET = {"si_k444": 1}
+SAMPLE_K = {"si_k444": [0, 21, 42], "si_k222_grad": [0, 5]}
+SEED_OFFSET = {"si_k444": 1, "si_k222_grad": 5}
 
 
 def inputs(name):
-    p = synth.WORKLOADS[name]()
+    p = synth.WORKLOADS[name]() if name in synth.WORKLOADS else synth.si_params(kmesh=(2, 2, 2))
     S = Setup(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"])
     c_phi, c_chi = synth.random_orbitals(synth.SEED0 + SEED_OFFSET[name], [S.kpG(k) for k in range(S.Nk)],
                                          S.npw_max, S.nbands)
@@ -40,7 +46,36 @@ def cplx_list(a):
     return [[float(x.real), float(x.imag)] for x in np.asarray(a).ravel()]
 
 
+def main_grad(name):
+    t0 = time.time()
+    p, S, c_phi, c_chi, occ = inputs(name)
+    ks = SAMPLE_K[name]
+    g_phi, g_chi = GR.orbital_gradient(S, c_phi, c_chi, occ)
+    pg = GR.param_gradient(S, c_phi, c_chi, occ)
+    E = OP.energy_terms(S, c_phi, c_chi, occ)["total"]
+    doc = {
+        "workload": name,
+        "source": "oracle/ (tests/golden/make_golden.py)",
+        "seed": synth.SEED0 + SEED_OFFSET[name],
+        "shape": [S.Nk, S.nbands, S.npw_max],
+        "sample_k": ks,
+        "input_probe": {"index": [[k, b, 5] for k in ks for b in range(S.nbands)],
+                        "phi": cplx_list([c_phi[k, b, 5] for k in ks for b in range(S.nbands)])},
+        "g_phi": {str(k): cplx_list(g_phi[k]) for k in ks},
+        "g_chi": {str(k): cplx_list(g_chi[k]) for k in ks},
+        "dE_dA": pg["A"],
+        "dE_dC": pg["C"],
+        "energy": E,
+        "oracle_seconds": time.time() - t0,
+    }
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(doc, f)
+    print("wrote", name, "in %.0f s" % (time.time() - t0))
+
+
 def main(name):
+    if name.endswith("_grad"):
+        return main_grad(name)
     t0 = time.time()
     p, S, c_phi, c_chi, occ = inputs(name)
     ks = SAMPLE_K[name]
