@@ -139,6 +139,15 @@ tc_status tc_energy(tc_ctx* ctx, const void* phi_R, const void* phi_L, const dou
 tc_status tc_energy_grad(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, void* dE_dphiR,
                          void* dE_dphiL, double dE_dA[2], double dE_dC[2], void* cuda_stream);
 
+/* Biorthonormalises right and left orbitals in place, per k-point (Sec. 2.1:
+ * <chi_i|phi_j> = delta_ij and <phi_i|phi_i> = 1; Sec. 2.3: Gram-Schmidt).
+ * phi_R is orthonormalised by modified Gram-Schmidt in band order; phi_L is
+ * replaced by chi_j = sum_i chi'_i (M^-1)_ij, M_ij = <phi_i|chi'_j> (FP64,
+ * partial pivoting), which keeps the span of the left set.  All nbands bands
+ * (at most 64).  Arrays may be host or device pointers; blocks the host.
+ * TC_ERR_ARG if a norm or a pivot vanishes (outputs then undefined). */
+tc_status tc_biorthonormalize(tc_ctx* ctx, void* phi_R, void* phi_L, void* cuda_stream);
+
 /* Batched 3D FFT of `batch` contiguous n^3 complex volumes in place on the
  * device (precision TC_FP64: complex128, TC_FP32: complex64), sign -1
  * (sum f e^{-2 pi i m.r/n}) or +1; unnormalised.  Exposes the library's

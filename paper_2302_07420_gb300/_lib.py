@@ -16,7 +16,8 @@ TERMS = ("2ah", "2bh1", "2bh2", "2ax", "2bx1", "2bx2", "3a1", "3a2", "3a3", "3a4
          "3b1", "3b2", "3b3", "3b4", "3b5", "3b6")
 TC_NTERMS = 17          # 16 operator terms + kinetic
 EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d",
-            "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad")
+            "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
+            "tc_biorthonormalize")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",
@@ -76,8 +77,10 @@ def load():
     lib.tc_apply_noalloc.argtypes = [ctypes.POINTER(tc_params), vp, vp, ctypes.POINTER(ctypes.c_double), vp, vp, vp]
     dp = ctypes.POINTER(ctypes.c_double)
     lib.tc_energy_grad.argtypes = [vp, vp, vp, dp, vp, vp, dp, dp, vp]
+    lib.tc_biorthonormalize.argtypes = [vp, vp, vp, vp]
     for name in ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
-                 "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad"):
+                 "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
+            "tc_biorthonormalize"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -83,13 +83,15 @@ template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t&
 void free_all(tc_ctx* c) {
   void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
                   c->d_hartU, c->d_hartUs, c->d_occ, c->d_phi, c->d_chi, c->d_gphi, c->d_gchi, c->d_side,
-                  c->d_cs, c->d_scratch, c->d_in_phi, c->d_in_chi, c->d_out_R, c->d_out_L, c->d_edot};
+                  c->d_cs, c->d_scratch, c->d_in_phi, c->d_in_chi, c->d_out_R, c->d_out_L, c->d_edot,
+                  c->d_npw, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->h_occ) cudaFreeHost(c->h_occ);
   if (c->h_edot) cudaFreeHost(c->h_edot);
+  if (c->h_status) cudaFreeHost(c->h_status);
 }
 
 // e[j] = sum_G conj(c_chi) (kin |k+G|^2/2 c_phi + out), FP64
@@ -143,6 +145,138 @@ __global__ void k_grad_combine(const double2* __restrict__ cphi, const double2* 
     if (gchi) {
       const double2 x = cphi[e], o = outR[e];
       gchi[e] = make_double2(w * (t * x.x + o.x), w * (t * x.y + o.y));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Biorthonormalisation per k-point (one CTA per k, FP64): modified Gram-Schmidt
+// of the right orbitals in band order, then chi_j <- sum_i chi_i (M^-1)_ij with
+// M_ij = <phi_i|chi_j> (Gauss-Jordan with partial pivoting on [M | I] in shared
+// memory), so that <chi_j|phi_l> = delta_jl.  *status = k + 1 if a norm or a
+// pivot vanishes at k-point k.
+constexpr int kBiorthoMaxBands = 64;
+
+__device__ double2 block_dot(const double2* a, const double2* b, int n, double* red) {
+  // sum_g conj(a_g) b_g over the CTA; result valid in every thread
+  double sx = 0.0, sy = 0.0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const double2 x = a[g], y = b[g];
+    sx += x.x * y.x + x.y * y.y;
+    sy += x.x * y.y - x.y * y.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+  }
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) { red[2 * w] = sx; red[2 * w + 1] = sy; }
+  __syncthreads();
+  double tx = 0.0, ty = 0.0;
+  for (int i = 0; i < nw; ++i) { tx += red[2 * i]; ty += red[2 * i + 1]; }
+  return make_double2(tx, ty);
+}
+
+__global__ void k_biortho(double2* phi, double2* chi, const int* __restrict__ npw_k, int npw_max, int nb, int* status) {
+  extern __shared__ double2 aug[];   // [nb][2 nb]
+  __shared__ double red[64];
+  __shared__ double2 fac[kBiorthoMaxBands];
+  __shared__ int piv;
+  __shared__ int bad;
+  const int k = blockIdx.x, n = npw_k[k], w2 = 2 * nb;
+  double2* P = phi + (size_t)k * nb * npw_max;
+  double2* X = chi + (size_t)k * nb * npw_max;
+  if (threadIdx.x == 0) bad = 0;
+  // 1. modified Gram-Schmidt of the rows of P
+  for (int i = 0; i < nb; ++i) {
+    double2* pi = P + (size_t)i * npw_max;
+    for (int j = 0; j < i; ++j) {
+      const double2* pj = P + (size_t)j * npw_max;
+      const double2 r = block_dot(pj, pi, n, red);
+      for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        const double2 a = pj[g];
+        pi[g].x -= r.x * a.x - r.y * a.y;
+        pi[g].y -= r.x * a.y + r.y * a.x;
+      }
+      __syncthreads();
+    }
+    const double nrm = sqrt(block_dot(pi, pi, n, red).x);
+    if (!(nrm > 0.0)) {
+      if (threadIdx.x == 0) *status = k + 1;
+      return;   // uniform across the CTA
+    }
+    for (int g = threadIdx.x; g < n; g += blockDim.x) { pi[g].x /= nrm; pi[g].y /= nrm; }
+    __syncthreads();
+  }
+  // 2. [M | I], M_ij = <phi_i|chi_j>
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) {
+      const double2 m = block_dot(P + (size_t)i * npw_max, X + (size_t)j * npw_max, n, red);
+      if (threadIdx.x == 0) {
+        aug[i * w2 + j] = m;
+        aug[i * w2 + nb + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      }
+    }
+  __syncthreads();
+  double mmax = 0.0;
+  for (int e = 0; e < nb * nb; ++e) mmax = fmax(mmax, hypot(aug[(e / nb) * w2 + e % nb].x, aug[(e / nb) * w2 + e % nb].y));
+  // 3. Gauss-Jordan
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x == 0) {
+      int p = c;
+      double best = -1.0;
+      for (int r = c; r < nb; ++r) {
+        const double v = hypot(aug[r * w2 + c].x, aug[r * w2 + c].y);
+        if (v > best) { best = v; p = r; }
+      }
+      piv = p;
+      if (!(best > 1e-13 * mmax)) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+      if (threadIdx.x == 0) *status = k + 1;
+      return;
+    }
+    const int p = piv;
+    if (p != c)
+      for (int e = threadIdx.x; e < w2; e += blockDim.x) {
+        const double2 t = aug[c * w2 + e];
+        aug[c * w2 + e] = aug[p * w2 + e];
+        aug[p * w2 + e] = t;
+      }
+    __syncthreads();
+    const double2 d = aug[c * w2 + c];
+    const double dd = d.x * d.x + d.y * d.y;
+    const double2 inv = make_double2(d.x / dd, -d.y / dd);
+    __syncthreads();
+    for (int e = threadIdx.x; e < w2; e += blockDim.x) {
+      const double2 a = aug[c * w2 + e];
+      aug[c * w2 + e] = make_double2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
+    }
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) fac[r] = aug[r * w2 + c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * w2; e += blockDim.x) {
+      const int r = e / w2, col = e % w2;
+      if (r == c) continue;
+      const double2 f = fac[r], a = aug[c * w2 + col];
+      aug[e].x -= f.x * a.x - f.y * a.y;
+      aug[e].y -= f.x * a.y + f.y * a.x;
+    }
+    __syncthreads();
+  }
+  // 4. chi_j(G) = sum_i chi_i(G) Minv_ij   (Minv in the right half of aug)
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    double2 x[kBiorthoMaxBands];
+    for (int i = 0; i < nb; ++i) x[i] = X[(size_t)i * npw_max + g];
+    for (int j = 0; j < nb; ++j) {
+      double sx = 0.0, sy = 0.0;
+      for (int i = 0; i < nb; ++i) {
+        const double2 m = aug[i * w2 + nb + j];
+        sx += x[i].x * m.x - x[i].y * m.y;
+        sy += x[i].x * m.y + x[i].y * m.x;
+      }
+      X[(size_t)j * npw_max + g] = make_double2(sx, sy);
     }
   }
 }
@@ -240,6 +374,10 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_out_R, orb));
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_out_L, orb));
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_edot, nj * sizeof(double2)));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_npw, S.npw.size() * sizeof(int)));
+  if (e == cudaSuccess) ok(cudaMemcpy(c->d_npw, S.npw.data(), S.npw.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_status, sizeof(int)));
+  if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_status, sizeof(int)));
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_edot, nj * sizeof(double2)));
   if (e != cudaSuccess) {
     const tc_status st = (e == cudaErrorMemoryAllocation) ? TC_ERR_OOM : TC_ERR_CUDA;
@@ -512,6 +650,38 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
     if (e != cudaSuccess) return cuda_fail(c, e, "table restore");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "tc_energy_grad");
+  return TC_OK;
+}
+
+tc_status tc_biorthonormalize(tc_ctx* c, void* phi, void* chi, void* stream) {
+  if (!c) return TC_ERR_STATE;
+  if (!phi || !chi) return fail(c, TC_ERR_ARG, "null orbital pointer");
+  const tc::Setup& S = c->S;
+  if (S.nb > kBiorthoMaxBands) return fail(c, TC_ERR_UNSUPPORTED, "tc_biorthonormalize supports at most 64 bands");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t orb = (size_t)S.Nk * S.nb * S.npw_max * sizeof(double2);
+  const bool hp = !is_device_ptr(phi), hc = !is_device_ptr(chi);
+  double2* dp = hp ? c->d_in_phi : static_cast<double2*>(phi);
+  double2* dc = hc ? c->d_in_chi : static_cast<double2*>(chi);
+  cudaError_t e = cudaSuccess;
+  if (hp && (e = cudaMemcpyAsync(dp, phi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+  if (hc && (e = cudaMemcpyAsync(dc, chi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
+  if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "status");
+  const size_t smem = (size_t)S.nb * 2 * S.nb * sizeof(double2);
+  if ((e = cudaFuncSetAttribute(k_biortho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return cuda_fail(c, e, "k_biortho attribute");
+  k_biortho<<<S.Nk, 256, smem, st>>>(dp, dc, c->d_npw, S.npw_max, S.nb, c->d_status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "k_biortho");
+  int status = 0;
+  if ((e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(c, e, "status");
+  if (hp && (e = cudaMemcpyAsync(phi, dp, orb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "download");
+  if (hc && (e = cudaMemcpyAsync(chi, dc, orb, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuda_fail(c, e, "download");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "tc_biorthonormalize");
+  status = *c->h_status;
+  if (status != 0)
+    return fail(c, TC_ERR_ARG, "biorthonormalisation: vanishing norm or singular overlap at k-point " +
+                                   std::to_string(status - 1) + " (outputs undefined)");
   return TC_OK;
 }
 

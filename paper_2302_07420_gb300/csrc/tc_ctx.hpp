@@ -36,6 +36,9 @@ struct tc_ctx {
   double2 *d_in_phi = nullptr, *d_in_chi = nullptr, *d_out_R = nullptr, *d_out_L = nullptr;
   double2* d_edot = nullptr;       // [Nk*nb]
   double2* h_edot = nullptr;       // pinned
+  int* d_npw = nullptr;            // [Nk]
+  int* d_status = nullptr;         // device status word (tc_biorthonormalize)
+  int* h_status = nullptr;         // pinned
   std::vector<int> npw_host;
   // derivative kernel data d/dA_pp, d/dA_ap, d/dC_pp, d/dC_ap (host, FP64), built by the first tc_energy_grad
   std::vector<tc::KernelData> dkd;

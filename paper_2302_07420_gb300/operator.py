@@ -15,6 +15,17 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _data_ptr(x):
+    """Pointer of a contiguous complex128 torch tensor (any device) or numpy array."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.complex128 or not x.flags.c_contiguous:
+            raise TypeError("orbital arrays must be C-contiguous complex128")
+        return ctypes.c_void_p(x.ctypes.data)
+    if not x.is_contiguous() or str(x.dtype) != "torch.complex128":
+        raise TypeError("orbital tensors must be contiguous complex128")
+    return ctypes.c_void_p(x.data_ptr())
+
+
 def _stream_handle(stream):
     if stream is None:
         import torch
@@ -129,6 +140,14 @@ class Context:
                                      dA, dC, _stream_handle(stream))
         _lib.check(self.lib, self.h, st)
         return (g_phi, g_chi, np.array(dA[:]) if params else None, np.array(dC[:]) if params else None)
+
+    def biorthonormalize(self, phi_R, phi_L, stream=None):
+        """In place: phi_R orthonormal (Gram-Schmidt), phi_L biorthonormal to it, per k (torch or numpy)."""
+        for x in (phi_R, phi_L):
+            self._check_orbitals(x)
+        st = self.lib.tc_biorthonormalize(self.h, _data_ptr(phi_R), _data_ptr(phi_L), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return phi_R, phi_L
 
     def profile(self, enable=True):
         """Enable (and reset) or disable per-stage device timing."""
