@@ -73,7 +73,7 @@ typedef struct {
   double lattice[3][3];   /* bohr, rows a_1, a_2, a_3 */
   int kmesh[3];           /* Gamma-centred Monkhorst-Pack mesh */
   double ecut_ha;         /* plane-wave sphere |k+G|^2/2 <= ecut_ha (Hartree) */
-  int fft[3];             /* FFT box; must be cubic, n in {9, 12, 15, 16, 24} */
+  int fft[3];             /* FFT box; cubic, n in {9, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 48} */
   int nbands;             /* bands per k (outputs) */
   int nocc;               /* occupied bands per k (partners), 0 < nocc <= nbands */
   double A[2];            /* Jastrow A (Eq. Jastrow) for [parallel, antiparallel] spins */

@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libtc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                   "-I" + os.path.join(HERE, "..", "include")]
-SIZES = (9, 12, 15, 16, 24)
+SIZES = (9, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 48)
 REALS = ("float", "double")
 
 

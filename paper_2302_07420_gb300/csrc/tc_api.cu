@@ -16,7 +16,7 @@ namespace {
 thread_local std::string g_init_err;   // reason of the last failed tc_init on this thread
 
 // Box sizes with compiled specialisations.
-#define TC_FOR_N(X) X(9) X(12) X(15) X(16) X(24)
+#define TC_FOR_N(X) X(9) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(48)
 
 template <typename T> int dispatch_prepare(tc_ctx* c, int n) {
 #define CASE(NN) \

@@ -5,6 +5,7 @@
 namespace tc {
 
 constexpr int NT = 16;   // operator terms, order of TC_TERM_* in tc.h
+constexpr int kSmemLimit = 227 * 1024;   // bytes of shared memory per CTA on sm_103a
 enum { T2AH, T2BH1, T2BH2, T2AX, T2BX1, T2BX2, T3A1, T3A2, T3A3, T3A4, T3B1, T3B2, T3B3, T3B4, T3B5, T3B6 };
 
 // Fields of one side.  Right side: ket = phi, bra = chi; left side: ket = chi,

@@ -20,9 +20,28 @@
 
 namespace tc {
 
+// Threads per CTA: one pencil per thread up to 384 pencils, two per thread up to
+// 24^3, and 256 threads (several pencils each, up to 255 registers) above.
 template <int N> struct Cfg {
-  static constexpr int threads = (N * N <= 384) ? ((N * N + 31) / 32) * 32 : ((N * N / 2 + 31) / 32) * 32;
+  static constexpr int threads = (N * N <= 384) ? ((N * N + 31) / 32) * 32
+                                                : (N <= 24 ? ((N * N / 2 + 31) / 32) * 32 : 256);
 };
+
+// Whether one n^3 work volume (padded layout) fits in a CTA's shared memory.
+template <typename T, int N> struct Fit {
+  static constexpr bool one = (size_t)Geo<N>::vol * sizeof(cplx<T>) + 1024 <= (size_t)kSmemLimit;
+};
+
+// Work volume of a single-volume kernel: shared memory when it fits, else this
+// CTA's volume in the global scratch gwork (one volume per CTA of the launch).
+template <typename T, int N> __device__ __forceinline__ cplx<T>* work_vol(unsigned char* smraw, cplx<T>* gwork) {
+  if constexpr (Fit<T, N>::one) {
+    return reinterpret_cast<cplx<T>*>(smraw);
+  } else {
+    const size_t b = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    return gwork + b * (size_t)Geo<N>::vol;
+  }
+}
 
 template <typename T, int N> __device__ __forceinline__ cplx<T>* vol_slot(const Params<T>& P, cplx<T>* smem, int slot,
                                                                            int nslots, bool force_global = false) {
@@ -57,10 +76,11 @@ template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
 
 // ---------------------------------------------------------------------------
 // Standalone batched 3D FFT (testing hook).
-template <typename T, int N, int S> __global__ void __launch_bounds__(Cfg<N>::threads) k_fft3d(cplx<T>* data) {
+template <typename T, int N, int S>
+__global__ void __launch_bounds__(Cfg<N>::threads) k_fft3d(cplx<T>* data, cplx<T>* gwork) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* V = work_vol<T, N>(smraw, gwork);
   cplx<T>* d = data + (size_t)blockIdx.x * G::nn;
   auto ld = [&](int a, int b, int c) { return d[G::gidx(a, b, c)]; };
   auto st = [&](int a, int b, int c, cplx<T> v) { d[G::gidx(a, b, c)] = v; };
@@ -75,10 +95,10 @@ template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::threads)
     k_orbitals(const double2* __restrict__ cphi, const double2* __restrict__ cchi, const int* __restrict__ box_index,
                const double* __restrict__ kpg, int npw_max, int nb, cplx<T>* phi, cplx<T>* chi, cplx<T>* gphi,
-               cplx<T>* gchi) {
+               cplx<T>* gchi, cplx<T>* gwork) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* V = work_vol<T, N>(smraw, gwork);
   const int j = blockIdx.x, comp = blockIdx.y, set = blockIdx.z;
   const int k = j / nb;
   const double2* c = (set == 0 ? cphi : cchi) + (size_t)j * npw_max;
@@ -135,7 +155,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
     k_spec_fwd(Params<T> P, int which) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* V = work_vol<T, N>(smraw, P.scratch);
   const SideArgs<T>& S = P.side[blockIdx.y];
   const int c = blockIdx.x;
   const cplx<T>* a;
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
     k_hartree_inv(Params<T> P, int kind) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* V = work_vol<T, N>(smraw, P.scratch);
   const SideArgs<T>& S = P.side[blockIdx.y];
   const int c = blockIdx.x;
   const T zero3[3] = {0, 0, 0};
@@ -653,7 +673,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
     k_finalize(Params<T> P, double2* outR, double2* outL, const int* __restrict__ box_index) {
   using G = Geo<N>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx<T>* V = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* V = work_vol<T, N>(smraw, P.scratch);
   const int side = blockIdx.y;
   const SideArgs<T>& S = P.side[side];
   double2* out = side == 0 ? outR : outL;

@@ -26,9 +26,10 @@ static __device__ __align__(256) unsigned char g_noalloc_arena[kNoallocBytes];
 
 std::mutex g_mu;
 void* g_arena_addr[kMaxDevices] = {};
-unsigned g_prepared[kMaxDevices] = {};   // bit (prec * 8 + size slot): kernel attributes and twiddles set
+unsigned g_prepared[kMaxDevices] = {};   // bit (prec * 16 + size slot): kernel attributes and twiddles set
 
-#define TC_FOR_N(X) X(0, 9) X(1, 12) X(2, 15) X(3, 16) X(4, 24)
+#define TC_FOR_N(X) \
+  X(0, 9) X(1, 12) X(2, 15) X(3, 16) X(4, 18) X(5, 20) X(6, 24) X(7, 25) X(8, 27) X(9, 30) X(10, 32) X(11, 48)
 
 template <typename T> int prepare(tc_ctx* c, int n) {
 #define CASE(SLOT, NN) \
@@ -179,7 +180,7 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
     std::lock_guard<std::mutex> lock(g_mu);
     base = static_cast<char*>(arena_address(dev, e));
     if (!base) return fail(TC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    const unsigned bit = 1u << ((f64 ? 0 : 8) + size_slot(S.n));
+    const unsigned bit = 1u << ((f64 ? 0 : 16) + size_slot(S.n));
     if (!(g_prepared[dev] & bit)) {
       const int r = f64 ? prepare<double>(&c, S.n) : prepare<float>(&c, S.n);
       if (r != TC_OK) return fail((tc_status)r, c.err);

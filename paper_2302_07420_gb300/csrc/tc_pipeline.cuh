@@ -1,5 +1,6 @@
 // Host-side launch sequence of the operator for one (precision, box size).
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -8,7 +9,6 @@
 
 namespace tc {
 
-constexpr int kSmemLimit = 227 * 1024;   // bytes of shared memory per CTA on sm_103a
 
 template <typename T> static inline size_t side_field_vols(int Nk, int nb, int no) {
   // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc  = 25
@@ -106,23 +106,29 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
     return TC_ERR_CUDA;
   }
   const int vb = vol_bytes<T, N>();
-  TC_SET_SMEM((k_orbitals<T, N>), vb);
-  TC_SET_SMEM((k_spec_fwd<T, N>), vb);
-  TC_SET_SMEM((k_hartree_inv<T, N>), vb);
-  TC_SET_SMEM((k_finalize<T, N>), vb);
+  const int vb1 = Fit<T, N>::one ? vb : 0;   // single-volume kernels: shared memory or global scratch
+  TC_SET_SMEM((k_orbitals<T, N>), vb1);
+  TC_SET_SMEM((k_spec_fwd<T, N>), vb1);
+  TC_SET_SMEM((k_hartree_inv<T, N>), vb1);
+  TC_SET_SMEM((k_finalize<T, N>), vb1);
   TC_SET_SMEM((k_occ_pairs<T, N>), (smem_vols<T, N>(4) * vb));
   TC_SET_SMEM((k_pair_chain<T, N>), (smem_vols<T, N>(3) * vb));
   TC_SET_SMEM((k_pair_3b4<T, N>), (smem_vols<T, N>(2) * vb));
-  TC_SET_SMEM((k_fft3d<T, N, -1>), vb);
-  TC_SET_SMEM((k_fft3d<T, N, +1>), vb);
+  TC_SET_SMEM((k_fft3d<T, N, -1>), vb1);
+  TC_SET_SMEM((k_fft3d<T, N, +1>), vb1);
   return TC_OK;
 }
 
+// Global scratch: the per-CTA volumes of k_occ_pairs (6) and k_pair_chain (3)
+// that are not in shared memory, and -- for boxes whose volume does not fit in
+// shared memory -- the work volume of every CTA of the single-volume kernels
+// (at most 8 per orbital in k_orbitals).  The uses never overlap in time.
 template <typename T, int N> size_t scratch_needed(const Setup& S) {
   const size_t vb = (size_t)vol_bytes<T, N>();
   const size_t a = (size_t)2 * S.Nk * S.no * 6 * vb;
   const size_t b = (size_t)2 * S.Nk * S.nb * 3 * vb;
-  return a > b ? a : b;
+  const size_t c = Fit<T, N>::one ? 0 : (size_t)8 * S.Nk * S.nb * vb;
+  return std::max(a, std::max(b, c));
 }
 
 #define TC_CHECK_LAUNCH(name)                                                                 \
@@ -160,30 +166,32 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   const auto& S = ctx->S;
   const int TH = Cfg<N>::threads;
   const int vb = vol_bytes<T, N>();
+  const int vb1 = Fit<T, N>::one ? vb : 0;
   Params<T> P = make_params<T, N>(ctx, tw);
   const int nj = S.Nk * S.nb;
   const int pw_blocks = 2 * 152;
   int nl[6] = {1, 9, 0, 1, 1, 1};   // kernel launches per stage
   // 1. orbitals to real space
   stage_mark(ctx, st, 0);
-  k_orbitals<T, N><<<dim3(nj, 4, 2), TH, vb, st>>>(cphi, cchi, ctx->d_box_index, ctx->d_kpg, S.npw_max, S.nb,
+  k_orbitals<T, N><<<dim3(nj, 4, 2), TH, vb1, st>>>(cphi, cchi, ctx->d_box_index, ctx->d_kpg, S.npw_max, S.nb,
                                                    (cplx<T>*)ctx->d_phi, (cplx<T>*)ctx->d_chi,
-                                                   (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi);
+                                                   (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi,
+                                                   (cplx<T>*)ctx->d_scratch);
   TC_CHECK_LAUNCH("k_orbitals");
   // 2. densities and Hartree-type fields
   stage_mark(ctx, st, 1);
   k_density<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_density");
-  k_spec_fwd<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 0);
-  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 1);
+  k_spec_fwd<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 0);
+  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 1);
   TC_CHECK_LAUNCH("k_spec_fwd");
-  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 0);
-  k_hartree_inv<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 1);
-  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 2);
-  k_hartree_inv<T, N><<<dim3(2, nsides), TH, vb, st>>>(P, 5);
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 0);
+  k_hartree_inv<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 1);
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 2);
+  k_hartree_inv<T, N><<<dim3(2, nsides), TH, vb1, st>>>(P, 5);
   TC_CHECK_LAUNCH("k_hartree_inv");
-  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 2);
-  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 3);
+  k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 2);
+  k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 3);
   TC_CHECK_LAUNCH("hartree 3b1");
   // 3. occupied-pair stage
   stage_mark(ctx, st, 2);
@@ -195,8 +203,8 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     TC_CHECK_LAUNCH("k_occ_pairs");
     k_reduce_a4<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(Pa);
     TC_CHECK_LAUNCH("k_reduce_a4");
-    k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb, st>>>(P, 3);
-    k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb, st>>>(P, 4);
+    k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 3);
+    k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 4);
     TC_CHECK_LAUNCH("hartree 3b2");
     nl[2] = 4;
   }
@@ -220,7 +228,7 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   }
   // 5. local terms, corrections, back to the sphere
   stage_mark(ctx, st, 5);
-  k_finalize<T, N><<<dim3(nj, nsides), TH, vb, st>>>(P, outR, outL, ctx->d_box_index);
+  k_finalize<T, N><<<dim3(nj, nsides), TH, vb1, st>>>(P, outR, outL, ctx->d_box_index);
   TC_CHECK_LAUNCH("k_finalize");
   stage_mark(ctx, st, 6);
   return stage_collect(ctx, 6, nl);
@@ -228,11 +236,16 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
 
 template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cudaStream_t st) {
   const int vb = vol_bytes<T, N>();
+  const int vb1 = Fit<T, N>::one ? vb : 0;
+  cplx<T>* gwork = nullptr;   // boxes too large for shared memory: stream-ordered work volumes
+  if (!Fit<T, N>::one && cudaMallocAsync((void**)&gwork, (size_t)batch * vb, st) != cudaSuccess) return TC_ERR_OOM;
   if (sign < 0)
-    k_fft3d<T, N, -1><<<batch, Cfg<N>::threads, vb, st>>>(reinterpret_cast<cplx<T>*>(data));
+    k_fft3d<T, N, -1><<<batch, Cfg<N>::threads, vb1, st>>>(reinterpret_cast<cplx<T>*>(data), gwork);
   else
-    k_fft3d<T, N, +1><<<batch, Cfg<N>::threads, vb, st>>>(reinterpret_cast<cplx<T>*>(data));
-  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+    k_fft3d<T, N, +1><<<batch, Cfg<N>::threads, vb1, st>>>(reinterpret_cast<cplx<T>*>(data), gwork);
+  const cudaError_t e = cudaGetLastError();
+  if (gwork) cudaFreeAsync(gwork, st);
+  return e == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
 #define TC_INSTANTIATE(T, N)                                                                             \

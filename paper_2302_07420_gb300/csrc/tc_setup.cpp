@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <iterator>
 #include <map>
 #include <tuple>
 
@@ -195,7 +196,9 @@ std::string build_setup(const tc_params& p, Setup& S) {
   S.prm = p;
   if (p.fft[0] != p.fft[1] || p.fft[1] != p.fft[2]) return "unsupported: FFT box must be cubic";
   const int n = p.fft[0];
-  if (!(n == 9 || n == 12 || n == 15 || n == 16 || n == 24)) return "unsupported: FFT box size (9, 12, 15, 16 or 24)";
+  static const int kSizes[] = {9, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 48};
+  if (std::find(std::begin(kSizes), std::end(kSizes), n) == std::end(kSizes))
+    return "unsupported: FFT box size (9, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32 or 48)";
   for (int i = 0; i < 3; ++i)
     if (p.kmesh[i] < 1 || p.kmesh[i] > 16) return "kmesh entries must be in [1, 16]";
   if (!(p.nocc > 0 && p.nocc <= p.nbands)) return "need 0 < nocc <= nbands";

@@ -41,7 +41,10 @@ def tiny_case(seed, kmesh, fft, nbands=3, nocc=2, fill=None, ecut=1.6, scale=5.0
     return p, S, c_phi, c_chi, occ
 
 
-@pytest.mark.parametrize("n", [9, 12, 15, 16, 24])
+SIZES = [9, 12, 15, 16, 18, 20, 24, 25, 27, 30, 32, 48]
+
+
+@pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("sign", [-1, 1])
 def test_fft3d_matches_numpy(n, prec, sign):
@@ -60,7 +63,7 @@ def test_fft3d_matches_numpy(n, prec, sign):
 @pytest.mark.parametrize("name", ["heg_14", "si_k444", "heg_114"])
 def test_layout_matches_oracle(name):
     p = synth.WORKLOADS[name]()
-    if p["fft"][0] not in (9, 12, 15, 16, 24):
+    if p["fft"][0] not in SIZES:
         pytest.skip("box size not compiled")
     S = make_setup(p)
     ctx = _ctx(p)
@@ -74,9 +77,12 @@ def test_layout_matches_oracle(name):
 
 
 CASES = [(0, (1, 1, 2), 9), (1, (2, 1, 1), 12), (2, (1, 2, 2), 15)]
+# boxes beyond 24^3 keep some or all work volumes in global memory instead of shared memory
+LARGE = [(3, (1, 1, 2), 18), (4, (1, 1, 1), 20), (5, (1, 2, 1), 25), (6, (1, 1, 2), 27), (7, (1, 1, 1), 30),
+         (8, (2, 1, 1), 32)]
 
 
-@pytest.mark.parametrize("seed,kmesh,fft", CASES)
+@pytest.mark.parametrize("seed,kmesh,fft", CASES + [LARGE[-1]])
 def test_parity_fp64_every_term(seed, kmesh, fft):
     p, S, c_phi, c_chi, occ = tiny_case(seed, kmesh, fft, fill=(1.0, 0.6))
     ref_r = OP.apply_operator(S, c_phi, c_chi, occ, left=False)
@@ -92,7 +98,7 @@ def test_parity_fp64_every_term(seed, kmesh, fft):
         assert er < TOL64 and el < TOL64, (t, er, el)
 
 
-@pytest.mark.parametrize("seed,kmesh,fft", CASES)
+@pytest.mark.parametrize("seed,kmesh,fft", CASES + LARGE)
 @pytest.mark.parametrize("prec,tol", [("fp64", TOL64), ("fp32", TOL32)])
 def test_parity_total(seed, kmesh, fft, prec, tol):
     p, S, c_phi, c_chi, occ = tiny_case(seed, kmesh, fft, fill=(1.0, 0.6))
