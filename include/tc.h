@@ -211,6 +211,39 @@ tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
 tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R, const void* phi_L, const double* occ,
                            void* out_R, void* out_L, void* cuda_stream);
 
+/* Batches of independent cells (many small problems of uneven size).
+ *
+ * tc_init_batch builds one context per cell (params[i]: each its own lattice,
+ * k mesh, cutoff, box, bands and Jastrow; every cell the same precision) that
+ * share one device workspace.  The workspace has L lanes, each as large as the
+ * largest cell needs; cells are assigned to lanes by estimated cost (longest
+ * first, least loaded lane), run one after another within a lane and
+ * concurrently across lanes.  tc_apply_batch applies the operator (both sides,
+ * as tc_apply) to every cell: the first call captures the whole schedule in a
+ * CUDA graph.  To choose L it first times graphs for L = 1, 2, 4, 8, 16 (as
+ * memory allows: a quarter of the free device memory) over a sample of at most
+ * 12 cells spread over the cost order, and keeps the fastest; later calls
+ * with the same arrays replay that graph with one launch on cuda_stream (new
+ * arrays: one new capture).  Arguments are arrays of ncell pointers: device
+ * orbital and output arrays in each cell's own layout, host occupations.
+ * tc_apply_batch waits for the previous replay to finish before it returns
+ * (the occupations are staged in pinned buffers); it does not wait for its own.
+ *
+ * tc_batch_cell returns cell i's context (owned by the batch: do not destroy
+ * it) for tc_layout, tc_setup_scalars and single-cell calls; those use the
+ * batch's workspace, so they must not overlap with a replay in flight.
+ * tc_batch_info reports the number of cells, the chosen lane count (0 before
+ * the first tc_apply_batch), the largest count memory allows, and the measured
+ * replay time in ms of the tuning sample for L = 1, 2, 4, 8, 16 (-1 where not
+ * tried).
+ * tc_destroy on the batch frees every cell.  Single-cell entry points return
+ * TC_ERR_STATE on a batch context. */
+tc_status tc_init_batch(int ncell, const tc_params* params, tc_ctx** out);
+tc_status tc_batch_cell(tc_ctx* batch, int i, tc_ctx** cell);
+tc_status tc_apply_batch(tc_ctx* batch, const void* const* phi_R, const void* const* phi_L, const double* const* occ,
+                         void* const* out_R, void* const* out_L, void* cuda_stream);
+tc_status tc_batch_info(const tc_ctx* batch, int* ncell, int* lanes, int* lanes_max, double* tune_ms);
+
 /* Reason of the last failure on ctx; with ctx == NULL, of the last failed
  * tc_init on the calling thread.  The string lives until the next call. */
 const char* tc_last_error(const tc_ctx* ctx);

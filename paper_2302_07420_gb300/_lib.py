@@ -17,7 +17,7 @@ TERMS = ("2ah", "2bh1", "2bh2", "2ax", "2bx1", "2bx2", "3a1", "3a2", "3a3", "3a4
 TC_NTERMS = 17          # 16 operator terms + kinetic
 EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d",
             "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
-            "tc_biorthonormalize")
+            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",
@@ -78,9 +78,14 @@ def load():
     dp = ctypes.POINTER(ctypes.c_double)
     lib.tc_energy_grad.argtypes = [vp, vp, vp, dp, vp, vp, dp, dp, vp]
     lib.tc_biorthonormalize.argtypes = [vp, vp, vp, vp]
+    lib.tc_init_batch.argtypes = [ip, ctypes.POINTER(tc_params), ctypes.POINTER(vp)]
+    lib.tc_batch_cell.argtypes = [vp, ip, ctypes.POINTER(vp)]
+    lib.tc_apply_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(dp),
+                                   ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    lib.tc_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), dp]
     for name in ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
                  "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
-            "tc_biorthonormalize"):
+            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

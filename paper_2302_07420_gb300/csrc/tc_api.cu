@@ -14,6 +14,7 @@ using tc::NT;
 namespace {
 
 thread_local std::string g_init_err;   // reason of the last failed tc_init on this thread
+void term_weights(const tc_ctx* c, double* tw, double two, double three);
 
 // Box sizes with compiled specialisations.
 #define TC_FOR_N(X) X(9) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(48)
@@ -82,9 +83,8 @@ template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t&
 
 void free_all(tc_ctx* c) {
   void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
-                  c->d_hartU, c->d_hartUs, c->d_occ, c->d_phi, c->d_chi, c->d_gphi, c->d_gchi, c->d_side,
-                  c->d_cs, c->d_scratch, c->d_in_phi, c->d_in_chi, c->d_out_R, c->d_out_L, c->d_edot,
-                  c->d_npw, c->d_status};
+                  c->d_hartU, c->d_hartUs, c->d_occ, c->ws_owned ? c->d_ws : nullptr, c->d_in_phi, c->d_in_chi,
+                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
@@ -302,27 +302,63 @@ namespace tc {
 void set_thread_error(const std::string& msg) { g_init_err = msg; }
 }  // namespace tc
 
-extern "C" {
+namespace tc {
 
-tc_status tc_init(const tc_params* params, tc_ctx** out) {
-  if (!params || !out) return TC_ERR_ARG;
+WsLayout ws_layout(const tc_ctx* c) {
+  const Setup& S = c->S;
+  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb, vol = NN * c->esz;
+  WsLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L.phi = take(nj * vol);
+  L.chi = take(nj * vol);
+  L.gphi = take(nj * 3 * vol);
+  L.gchi = take(nj * 3 * vol);
+  L.side_bytes = (25 + (size_t)S.Nk * S.no * 9 + nj * 7) * vol;   // see fill_side
+  L.side = take(2 * L.side_bytes);
+  L.cs_bytes = (size_t)2 * nj * S.no * 6 * sizeof(double);
+  L.cs = take(L.cs_bytes);
+  L.scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n) : dispatch_scratch<float>(S, S.n);
+  L.scratch = take(L.scratch_bytes);
+  L.total = (off + 255) & ~(size_t)255;
+  return L;
+}
+
+void ws_assign(tc_ctx* c, char* base, const WsLayout& L) {
+  c->d_phi = base + L.phi;
+  c->d_chi = base + L.chi;
+  c->d_gphi = base + L.gphi;
+  c->d_gchi = base + L.gchi;
+  c->d_side = base + L.side;
+  c->side_bytes = L.side_bytes;
+  c->d_cs = reinterpret_cast<double*>(base + L.cs);
+  c->d_scratch = base + L.scratch;
+  c->scratch_bytes = L.scratch_bytes;
+}
+
+int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std::string& err) {
   *out = nullptr;
   tc_ctx* c = new (std::nothrow) tc_ctx();
-  if (!c) return TC_ERR_OOM;
+  if (!c) { err = "host allocation failed"; return TC_ERR_OOM; }
   std::string why = tc::build_setup(*params, c->S);
-  g_init_err = why;
   if (!why.empty()) {
-    const tc_status st = why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
+    err = why;
     delete c;
-    return st;
+    return why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
   }
   tc::Setup& S = c->S;
   c->prec = params->precision;
   c->esz = c->prec == TC_FP64 ? 16 : 8;
+  c->ws_owned = own_workspace;
   cudaGetDevice(&c->device);
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; return r == cudaSuccess; };
-  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb;
+  const size_t nj = (size_t)S.Nk * S.nb;
   // basis
   ok(cudaMalloc((void**)&c->d_box_index, S.box_index.size() * sizeof(int)));
   if (e == cudaSuccess) ok(cudaMemcpy(c->d_box_index, S.box_index.data(), S.box_index.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -354,20 +390,13 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
   c->d_hartUs = up(S.hartUs);
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_occ, nj * sizeof(double)));
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_occ, nj * sizeof(double)));
-  // fields and workspace
-  const size_t vol = NN * c->esz;
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_phi, nj * vol));
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_chi, nj * vol));
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_gphi, nj * 3 * vol));
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_gchi, nj * 3 * vol));
-  const size_t side_vols = 25 + (size_t)S.Nk * S.no * 9 + nj * 7;   // see fill_side
-  c->side_bytes = side_vols * vol;
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_side, 2 * c->side_bytes));
-  if (e == cudaSuccess) ok(cudaMemset(c->d_side, 0, 2 * c->side_bytes));
-  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_cs, (size_t)2 * nj * S.no * 6 * sizeof(double)));
-  if (e == cudaSuccess) ok(cudaMemset(c->d_cs, 0, (size_t)2 * nj * S.no * 6 * sizeof(double)));
-  c->scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n) : dispatch_scratch<float>(S, S.n);
-  if (e == cudaSuccess) ok(cudaMalloc(&c->d_scratch, c->scratch_bytes));
+  // workspace: real-space fields, per-side fields, correction scalars, scratch (zeroed once)
+  if (own_workspace) {
+    const WsLayout L = ws_layout(c);
+    if (e == cudaSuccess) ok(cudaMalloc(&c->d_ws, L.total));
+    if (e == cudaSuccess) ok(cudaMemset(c->d_ws, 0, L.total));
+    if (e == cudaSuccess) ws_assign(c, static_cast<char*>(c->d_ws), L);
+  }
   const size_t orb = nj * S.npw_max * sizeof(double2);
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_in_phi, orb));
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_in_chi, orb));
@@ -380,26 +409,52 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_status, sizeof(int)));
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_edot, nj * sizeof(double2)));
   if (e != cudaSuccess) {
-    const tc_status st = (e == cudaErrorMemoryAllocation) ? TC_ERR_OOM : TC_ERR_CUDA;
-    g_init_err = std::string("tc_init: ") + cudaGetErrorString(e);
+    err = std::string("tc_init: ") + cudaGetErrorString(e);
     free_all(c);
     delete c;
-    return st;
+    return (e == cudaErrorMemoryAllocation) ? TC_ERR_OOM : TC_ERR_CUDA;
   }
   const int r = c->prec == TC_FP64 ? dispatch_prepare<double>(c, S.n) : dispatch_prepare<float>(c, S.n);
   if (r != TC_OK) {
-    g_init_err = c->err;
+    err = c->err;
     free_all(c);
     delete c;
-    return (tc_status)r;
+    return r;
   }
   c->npw_host = S.npw;
   *out = c;
   return TC_OK;
 }
 
+void destroy_context(tc_ctx* c) {
+  if (!c) return;
+  if (c->batch) destroy_batch(c);
+  free_all(c);
+  delete c;
+}
+
+int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st) {
+  double tw[NT];
+  term_weights(c, tw, 1.0, 1.0);
+  return c->prec == TC_FP64 ? dispatch_run<double>(c, phi, chi, outR, outL, tw, 2, st)
+                            : dispatch_run<float>(c, phi, chi, outR, outL, tw, 2, st);
+}
+
+}  // namespace tc
+
+extern "C" {
+
+tc_status tc_init(const tc_params* params, tc_ctx** out) {
+  if (!params || !out) return TC_ERR_ARG;
+  std::string err;
+  const int r = tc::init_context(params, true, out, err);
+  g_init_err = err;
+  return (tc_status)r;
+}
+
 tc_status tc_layout(const tc_ctx* c, int* nk, int* npw_max, const int** npw_per_k, const int** miller) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return TC_ERR_STATE;
   if (nk) *nk = c->S.Nk;
   if (npw_max) *npw_max = c->S.npw_max;
   if (npw_per_k) *npw_per_k = c->npw_host.data();
@@ -409,6 +464,7 @@ tc_status tc_layout(const tc_ctx* c, int* nk, int* npw_max, const int** npw_per_
 
 tc_status tc_setup_scalars(const tc_ctx* c, double out4[4]) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return TC_ERR_STATE;
   if (!out4) return TC_ERR_ARG;
   out4[0] = c->S.Omega;
   out4[1] = c->S.alpha;
@@ -476,17 +532,24 @@ static tc_status energy_reduce(tc_ctx* c, const double2* dphi, const double2* dc
   return TC_OK;
 }
 
-static void term_weights(const tc_ctx* c, double* tw, double two, double three) {
+}  // extern "C"
+
+namespace {
+void term_weights(const tc_ctx* c, double* tw, double two, double three) {
   const unsigned mask = c->S.prm.term_mask;
   for (int t = 0; t < NT; ++t) {
     const bool on = mask == 0u || (mask >> t) & 1u;
     tw[t] = on ? (t < 6 ? two : three) : 0.0;
   }
 }
+}  // namespace
+
+extern "C" {
 
 tc_status tc_apply(tc_ctx* c, const void* phi, const void* chi, const double* occ, void* outR, void* outL,
                    void* stream) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
   if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
   if (!outR && !outL) return TC_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -505,6 +568,7 @@ tc_status tc_apply(tc_ctx* c, const void* phi, const void* chi, const double* oc
 tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* occ, double* E_total,
                     double* E_terms, void* stream) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
   if (!phi || !chi || !occ || !E_total) return fail(c, TC_ERR_ARG, "null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const tc::Setup& S = c->S;
@@ -549,6 +613,7 @@ tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* o
 tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const double* occ, void* dE_dphiR,
                          void* dE_dphiL, double* dE_dA, double* dE_dC, void* stream) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
   if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tc::Setup& S = c->S;
@@ -655,6 +720,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
 
 tc_status tc_biorthonormalize(tc_ctx* c, void* phi, void* chi, void* stream) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
   if (!phi || !chi) return fail(c, TC_ERR_ARG, "null orbital pointer");
   const tc::Setup& S = c->S;
   if (S.nb > kBiorthoMaxBands) return fail(c, TC_ERR_UNSUPPORTED, "tc_biorthonormalize supports at most 64 bands");
@@ -699,6 +765,7 @@ tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* 
 
 tc_status tc_profile(tc_ctx* c, int enable) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
   for (int i = 0; i < 8; ++i) {
     c->stage_ms[i] = 0.0;
     c->stage_launch[i] = 0;
@@ -713,6 +780,7 @@ tc_status tc_profile(tc_ctx* c, int enable) {
 
 tc_status tc_stage_times(const tc_ctx* c, double* ms, int* launches, int n) {
   if (!c) return TC_ERR_STATE;
+  if (c->batch) return TC_ERR_STATE;
   if (!ms || n < TC_NSTAGES) return TC_ERR_ARG;
   for (int i = 0; i < TC_NSTAGES; ++i) {
     ms[i] = c->stage_ms[i];
@@ -725,8 +793,8 @@ const char* tc_last_error(const tc_ctx* c) { return c ? c->err.c_str() : g_init_
 
 tc_status tc_destroy(tc_ctx* c) {
   if (!c) return TC_ERR_STATE;
-  free_all(c);
-  delete c;
+  if (c->batch_owner) return fail(c, TC_ERR_STATE, "this context belongs to a batch: destroy the batch");
+  tc::destroy_context(c);
   return TC_OK;
 }
 

@@ -6,6 +6,15 @@
 
 #include "tc_setup.hpp"
 
+namespace tc {
+struct BatchState;
+// Offsets of the workspace pieces of one context inside its workspace block.
+struct WsLayout {
+  size_t phi, chi, gphi, gchi, side, cs, scratch, total;
+  size_t side_bytes, cs_bytes, scratch_bytes;
+};
+}  // namespace tc
+
 struct tc_ctx {
   tc::Setup S;
   int prec = TC_FP64;
@@ -32,6 +41,9 @@ struct tc_ctx {
   double* d_cs = nullptr;          // [2][Nk*nb][no][6]
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
+  // workspace block holding d_phi .. d_scratch (owned unless the context belongs to a batch)
+  void* d_ws = nullptr;
+  bool ws_owned = true;
   // staging for host pointers and energy
   double2 *d_in_phi = nullptr, *d_in_chi = nullptr, *d_out_R = nullptr, *d_out_L = nullptr;
   double2* d_edot = nullptr;       // [Nk*nb]
@@ -42,6 +54,9 @@ struct tc_ctx {
   std::vector<int> npw_host;
   // derivative kernel data d/dA_pp, d/dA_ap, d/dC_pp, d/dC_ap (host, FP64), built by the first tc_energy_grad
   std::vector<tc::KernelData> dkd;
+  // batch contexts (tc_init_batch): the cells and their shared workspace; nullptr otherwise
+  tc::BatchState* batch = nullptr;
+  bool batch_owner = false;        // a cell of a batch (destroyed with the batch)
   // profiling (tc_profile / tc_stage_times)
   bool profile = false;
   cudaEvent_t ev[8] = {};
@@ -50,6 +65,18 @@ struct tc_ctx {
 };
 
 namespace tc {
+// Context construction without the public wrapper: all tables, staging buffers
+// and -- if own_workspace -- the workspace block.  Returns a tc_status; on
+// failure *out is null and err holds the reason.
+int init_context(const tc_params* p, bool own_workspace, tc_ctx** out, std::string& err);
+void destroy_context(tc_ctx* c);
+WsLayout ws_layout(const tc_ctx* c);
+void ws_assign(tc_ctx* c, char* base, const WsLayout& L);
+// Both operator sides into outR / outL (device pointers) on st, all terms of term_mask.
+int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st);
+void destroy_batch(tc_ctx* c);
+void set_thread_error(const std::string& msg);
+
 // Runs the operator pipeline on the given stream.  tw: per-term weights;
 // nsides: 2 (right and left) or 1 (right only).
 template <typename T, int N>

@@ -182,3 +182,73 @@ def fft3d(x, sign, stream=None):
     st = lib.tc_fft3d(n, prec, int(sign), _ptr(x), batch, _stream_handle(stream))
     _lib.check(lib, None, st)
     return x
+
+
+class BatchContext:
+    """tc_init_batch: many independent cells sharing one workspace, applied by one graph launch.
+
+    ``cells`` is a list of dicts with the Context arguments (lattice, kmesh, ecut,
+    fft, nbands, nocc, A, C and optionally alpha, div_correction, ushort_factor,
+    term_mask); every cell uses ``precision``.
+    """
+
+    def __init__(self, cells, precision="fp32"):
+        self.lib = _lib.load()
+        keys = ("lattice", "kmesh", "ecut", "fft", "nbands", "nocc", "A", "C")
+        opt = ("alpha", "div_correction", "ushort_factor", "term_mask")
+        prm = [_lib.make_params(*[c[k] for k in keys], **{k: c[k] for k in opt if k in c}, precision=precision)
+               for c in cells]
+        self.params = (_lib.tc_params * len(prm))(*prm)
+        h = ctypes.c_void_p()
+        st = self.lib.tc_init_batch(len(prm), self.params, ctypes.byref(h))
+        if st != _lib.TC_OK:
+            msg = self.lib.tc_last_error(None)
+            raise _lib.TCError(st, msg.decode() if msg else "tc_init_batch failed")
+        self.h = h
+        self.ncell = len(prm)
+        self.layouts = []
+        for i in range(self.ncell):
+            ch = ctypes.c_void_p()
+            _lib.check(self.lib, self.h, self.lib.tc_batch_cell(self.h, i, ctypes.byref(ch)))
+            nk, npw_max = ctypes.c_int(), ctypes.c_int()
+            pn = ctypes.POINTER(ctypes.c_int)()
+            pm = ctypes.POINTER(ctypes.c_int)()
+            _lib.check(self.lib, ch, self.lib.tc_layout(ch, ctypes.byref(nk), ctypes.byref(npw_max), ctypes.byref(pn),
+                                                        ctypes.byref(pm)))
+            npw = np.ctypeslib.as_array(pn, shape=(nk.value,)).copy()
+            miller = np.ctypeslib.as_array(pm, shape=(nk.value, npw_max.value, 3)).copy()
+            self.layouts.append((nk.value, npw_max.value, npw, miller))
+
+    def apply(self, phi_R, phi_L, occ, out_R=None, out_L=None, stream=None):
+        """Lists of per-cell complex128 cuda tensors in, lists out (both operator sides)."""
+        import torch
+        n = self.ncell
+        out_R = out_R if out_R is not None else [torch.empty_like(x) for x in phi_R]
+        out_L = out_L if out_L is not None else [torch.empty_like(x) for x in phi_L]
+        vp = ctypes.c_void_p
+        occs = [np.ascontiguousarray(np.asarray(o, dtype=np.float64)) for o in occ]
+        dpp = ctypes.POINTER(ctypes.c_double)
+        arrs = [(vp * n)(*[vp(x.data_ptr()) for x in xs]) for xs in (phi_R, phi_L, out_R, out_L)]
+        occ_arr = (dpp * n)(*[o.ctypes.data_as(dpp) for o in occs])
+        st = self.lib.tc_apply_batch(self.h, arrs[0], arrs[1], occ_arr, arrs[2], arrs[3], _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return out_R, out_L
+
+    def info(self):
+        """(ncell, chosen lanes, largest lane count, {lanes: measured replay ms})."""
+        nc, ln, lm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 5)()
+        _lib.check(self.lib, self.h, self.lib.tc_batch_info(self.h, ctypes.byref(nc), ctypes.byref(ln),
+                                                            ctypes.byref(lm), ms))
+        return nc.value, ln.value, lm.value, {L: ms[i] for i, L in enumerate((1, 2, 4, 8, 16)) if ms[i] >= 0}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

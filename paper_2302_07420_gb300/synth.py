@@ -17,6 +17,8 @@ Workloads (all in Hartree atomic units):
 * ``heg_114``  -- HEG, N = 114 electrons (57 plane waves, |n|^2 <= 5), r_s = 2,
   Gamma only, box 48^3, sphere |n|^2 <= 144.
 * ``tiny_*``   -- small random cells for brute-force checks.
+* ``heg_batch`` -- many independent HEG cells of uneven size (box 16^3-32^3,
+  1-8 k-points, 7-33 occupied plane waves per k), see ``heg_batch``.
 
 Jastrow parameters follow Eqs. A_normalize and cusp: A = sqrt(Omega/(4 pi N)),
 C_pp = sqrt(2 A), C_ap = sqrt(A).
@@ -121,6 +123,50 @@ def heg_orbitals(miller0, npw_max, radius2_occ):
     for b, i in enumerate(order):
         c[0, b, i] = 1.0
     return c
+
+
+def heg_kpoint_orbitals(kpg_list, miller_list, npw_max, nocc):
+    """Unit plane waves e^{i(k+G).r}: at every k the nocc lowest |k+G|^2 of the sphere.
+
+    Ties are broken by (|k+G|^2, m1, m2, m3); returns c (Nk, nocc, npw_max).
+    """
+    Nk = len(kpg_list)
+    c = np.zeros((Nk, nocc, npw_max), dtype=np.complex128)
+    for k in range(Nk):
+        kpg, m = np.asarray(kpg_list[k]), np.asarray(miller_list[k])
+        q2 = np.einsum("ij,ij->i", kpg, kpg)
+        order = sorted(range(len(q2)), key=lambda i: (round(q2[i], 12), m[i, 0], m[i, 1], m[i, 2]))
+        if len(order) < nocc:
+            raise ValueError("sphere holds fewer plane waves than occupied bands")
+        for b, i in enumerate(order[:nocc]):
+            c[k, b, i] = 1.0
+    return c
+
+
+HEG_BATCH_N = (14, 38, 54, 66)
+HEG_BATCH_BOX = (16, 18, 20, 24, 25, 27, 30, 32)
+HEG_BATCH_KMESH = ((1, 1, 1), (1, 1, 2), (1, 2, 2), (2, 2, 2))
+
+
+def heg_batch(ncell=256, index=4):
+    """Independent HEG cells: N uniform in {14, 38, 54, 66}, r_s uniform in [1, 5],
+    box uniform in {16, 18, 20, 24, 25, 27, 30, 32}, k mesh uniform in
+    {1x1x1, 1x1x2, 1x2x2, 2x2x2}; nbands = nocc = N/2, plane-wave sphere
+    |m|_2 <= floor((n - 1)/4) in index units (r = floor((n-1)/4)), A and C from
+    Eqs. A_normalize and cusp.  Seed 230207420 + index."""
+    rng = np.random.default_rng(SEED0 + index)
+    cells = []
+    for _ in range(ncell):
+        nelec = int(rng.choice(HEG_BATCH_N))
+        rs = float(rng.uniform(1.0, 5.0))
+        n = int(rng.choice(HEG_BATCH_BOX))
+        kmesh = tuple(HEG_BATCH_KMESH[int(rng.integers(len(HEG_BATCH_KMESH)))])
+        r = (n - 1) // 4
+        p = heg_params(nelec, rs, n, r * r)
+        p["kmesh"] = kmesh
+        p["ecut"] = 0.5 * (r * 2.0 * np.pi / p["lattice"][0, 0]) ** 2 * (1.0 + 1e-9)
+        cells.append(p)
+    return cells
 
 
 def occupations(Nk, nbands, nocc, fill=1.0):
