@@ -60,6 +60,31 @@ template <typename T, int N> __device__ __forceinline__ void pvec(const Params<T
   for (int d = 0; d < 3; ++d) p[d] = dl[d] + r1 * P.Bm[0][d] + r2 * P.Bm[1][d] + r3 * P.Bm[2][d];
 }
 
+// One Cartesian component d of p = Delta + G, with the per-component constants
+// taken out of the element loop: p_d = c0 + r1 b1 + r2 b2 + r3 b3 (r_i the
+// Miller integers of the FFT index).  Selecting the constants by d with
+// constant indices keeps every array access static (no local-memory copies).
+template <typename T> struct PComp {
+  T c0, b1, b2, b3;
+};
+
+template <typename T>
+__device__ __forceinline__ PComp<T> pcomp_setup(const Params<T>& P, const T* dl, int d) {
+  PComp<T> q;
+  q.c0 = dl ? dl[d] : T(0);
+  q.b1 = d == 0 ? P.Bm[0][0] : (d == 1 ? P.Bm[0][1] : P.Bm[0][2]);
+  q.b2 = d == 0 ? P.Bm[1][0] : (d == 1 ? P.Bm[1][1] : P.Bm[1][2]);
+  q.b3 = d == 0 ? P.Bm[2][0] : (d == 1 ? P.Bm[2][1] : P.Bm[2][2]);
+  return q;
+}
+
+template <typename T, int N> __device__ __forceinline__ T pcomp(const PComp<T>& q, int i1, int i2, int i3) {
+  const T r1 = (T)(i1 <= (N - 1) / 2 ? i1 : i1 - N);
+  const T r2 = (T)(i2 <= (N - 1) / 2 ? i2 : i2 - N);
+  const T r3 = (T)(i3 <= (N - 1) / 2 ? i3 : i3 - N);
+  return q.c0 + r1 * q.b1 + r2 * q.b2 + r3 * q.b3;
+}
+
 template <typename T> __device__ __forceinline__ cplx<T> ld(const cplx<T>* p, size_t i) { return p[i]; }
 
 template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
@@ -195,6 +220,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
   const SideArgs<T>& S = P.side[blockIdx.y];
   const int c = blockIdx.x;
   const T zero3[3] = {0, 0, 0};
+  const PComp<T> qc = pcomp_setup<T>(P, nullptr, kind == 1 ? c : 0);
   cplx<T>* dst = kind == 0 ? S.vH : kind == 1 ? S.h1 + (size_t)c * G::nn : kind == 2 ? S.vb2 : kind == 3 ? S.t3b1
                : kind == 4 ? S.t3b2 : S.vu + (size_t)c * G::nn;
   inv3d<T, N>(
@@ -203,13 +229,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
         const int g = G::gidx(i, j, k);
         if (kind == 0) return P.hartV[(size_t)S.side * G::nn + g] * S.nt[g];
         if (kind == 5) return P.hartUs[(size_t)c * G::nn + g] * S.nt[g];
-        T p[3];
-        pvec<T, N>(P, zero3, i, j, k, p);
         const T u = P.hartU[g];
         if (kind == 1) {
-          const cplx<T> t = (p[c] * u) * S.nt[g];
+          const cplx<T> t = (pcomp<T, N>(qc, i, j, k) * u) * S.nt[g];
           return mul_si<T, 1>(t);
         }
+        T p[3];
+        pvec<T, N>(P, zero3, i, j, k, p);
         const cplx<T>* src = (kind == 2) ? S.mt : S.spec;
         cplx<T> s = {0, 0};
 #pragma unroll
@@ -293,24 +319,21 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
       }
       for (int sp = 0; sp < 2; ++sp) {
         for (int d = 0; d < 3; ++d) {
+          const PComp<T> q21 = pcomp_setup<T>(P, d21, d), q12 = pcomp_setup<T>(P, d12, d);
           // B1 = P^s_d(q2, q1) (stored), B2 = P^s_d(q1, q2) (consumed with B1 in the last pass)
           inv3d<T, N>(
               B1,
               [&](int i, int j, int k) {
-                T p[3];
-                pvec<T, N>(P, d21, i, j, k, p);
                 const T u = P.tabU[((size_t)id21 * 2 + sp) * NN + G::gidx(i, j, k)];
-                return mul_si<T, 1>((p[d] * u) * A1[G::sidx(i, j, k)]);
+                return mul_si<T, 1>((pcomp<T, N>(q21, i, j, k) * u) * A1[G::sidx(i, j, k)]);
               },
               [&](int i, int j, int k, cplx<T> v) { B1[G::sidx(i, j, k)] = v; });
           struct Old3 { cplx<T> h6, a, b; };
           inv3d_rmw<T, N, 8>(
               B2,
               [&](int i, int j, int k) {
-                T p[3];
-                pvec<T, N>(P, d12, i, j, k, p);
                 const T u = P.tabU[((size_t)id12 * 2 + sp) * NN + G::gidx(i, j, k)];
-                return mul_si<T, 1>((p[d] * u) * A2[G::sidx(i, j, k)]);
+                return mul_si<T, 1>((pcomp<T, N>(q12, i, j, k) * u) * A2[G::sidx(i, j, k)]);
               },
               [&](int i, int j, int k) {
                 const int g = G::gidx(i, j, k);
@@ -526,12 +549,11 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
         const T* Ut = sp == 0 ? Upp : Uap;
         for (int d = 0; d < 3; ++d) {
           const bool first_C = (sp == 0 && d == 0);
+          const PComp<T> qd = pcomp_setup<T>(P, dl, d);
           // b = FT^{-1}[U_d A]: axes 2 and 3 here, axis 1 fused below
           fft_pass<T, N, +1, 2>(
               [&](int a, int b, int c) {
-                T p[3];
-                pvec<T, N>(P, dl, a, b, c, p);
-                return mul_si<T, 1>((p[d] * Ut[G::gidx(a, b, c)]) * A[G::sidx(a, b, c)]);
+                return mul_si<T, 1>((pcomp<T, N>(qd, a, b, c) * Ut[G::gidx(a, b, c)]) * A[G::sidx(a, b, c)]);
               },
               [&](int a, int b, int c, cplx<T> v) { B[G::sidx(a, b, c)] = v; });
           __syncthreads();
@@ -588,10 +610,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
           __syncthreads();
           fft_pass<T, N, -1, 2>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
                                 [&](int a, int b, int c, cplx<T> v) {
-                                  T p[3];
-                                  pvec<T, N>(P, dl, a, b, c, p);
                                   // -U_d FT[F] = -i p_d u (v / N)
-                                  const cplx<T> t = mul_si<T, -1>((p[d] * Ut[G::gidx(a, b, c)] * P.invN) * v);
+                                  const cplx<T> t =
+                                      mul_si<T, -1>((pcomp<T, N>(qd, a, b, c) * Ut[G::gidx(a, b, c)] * P.invN) * v);
                                   const int s = G::sidx(a, b, c);
                                   C[s] = first_C ? t : C[s] + t;
                                 });
@@ -640,13 +661,12 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
       const cplx<T>* braq = S.bra + (size_t)q * NN;
       const cplx<T>* ketq = S.ket + (size_t)q * NN;
       for (int d = 0; d < 3; ++d) {
+        const PComp<T> qd = pcomp_setup<T>(P, dl, d);
         fwd3d<T, N>(
             B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(w + d * NN + g), ldg(braq + g)); },
             [&](int a, int b, int c, cplx<T> v) {
-              T p[3];
-              pvec<T, N>(P, dl, a, b, c, p);
               // -U_d FT[-conj(bra_q) w_d] = +i p_d u FT[conj(bra_q) w_d]
-              const cplx<T> t = mul_si<T, 1>((p[d] * Upp[G::gidx(a, b, c)] * P.invN) * v);
+              const cplx<T> t = mul_si<T, 1>((pcomp<T, N>(qd, a, b, c) * Upp[G::gidx(a, b, c)] * P.invN) * v);
               const int s = G::sidx(a, b, c);
               A[s] = d == 0 ? t : A[s] + t;
             });
