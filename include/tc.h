@@ -190,7 +190,9 @@ tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
  * Sizes: a problem whose buffers exceed TC_NOALLOC_MAX_BYTES is rejected with
  * TC_ERR_UNSUPPORTED before any device work; tc_last_error(NULL) states the
  * bytes it would need (a 16^3 box with 7 bands at one k-point in FP64 needs
- * about 30 MB).
+ * about 30 MB).  Where the partner chunking that tc_init would choose (several
+ * partial accumulators per orbital, for a fuller last wave of CTAs) does not
+ * fit, the call runs with one chunk.
  *
  * Arguments: phi_R, phi_L, out_R, out_L must be device pointers (host
  * pointers give TC_ERR_ARG); out_R or out_L may be NULL to skip that side.

@@ -27,9 +27,9 @@ template <typename T> int dispatch_prepare(tc_ctx* c, int n) {
   return TC_ERR_UNSUPPORTED;
 }
 
-template <typename T> size_t dispatch_scratch(const tc::Setup& S, int n) {
+template <typename T> size_t dispatch_scratch(const tc::Setup& S, int n, int so_max, int sc_max) {
 #define CASE(NN) \
-  case NN: return tc::scratch_needed<T, NN>(S);
+  case NN: return tc::scratch_needed<T, NN>(S, so_max, sc_max);
   switch (n) { TC_FOR_N(CASE) }
 #undef CASE
   return 0;
@@ -319,14 +319,55 @@ WsLayout ws_layout(const tc_ctx* c) {
   L.chi = take(nj * vol);
   L.gphi = take(nj * 3 * vol);
   L.gchi = take(nj * 3 * vol);
-  L.side_bytes = (25 + (size_t)S.Nk * S.no * 9 + nj * 7) * vol;   // see fill_side
+  L.side_bytes = side_field_vols(S.Nk, S.nb, S.no, c->so_max, c->sc_max) * vol;
   L.side = take(2 * L.side_bytes);
   L.cs_bytes = (size_t)2 * nj * S.no * 6 * sizeof(double);
   L.cs = take(L.cs_bytes);
-  L.scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n) : dispatch_scratch<float>(S, S.n);
+  L.scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n, c->so_max, c->sc_max)
+                                       : dispatch_scratch<float>(S, S.n, c->so_max, c->sc_max);
   L.scratch = take(L.scratch_bytes);
   L.total = (off + 255) & ~(size_t)255;
   return L;
+}
+
+size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max) {
+  // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc = 25; per occupied
+  // state h3a4(3) and h3b(3) per chunk part and Z(3); per orbital acc(1) and w(3) per part and Y(3)
+  return 25 + (size_t)Nk * no * 3 * (2 * (size_t)so_max + 1) + (size_t)Nk * nb * (4 * (size_t)sc_max + 3);
+}
+
+// Number of partner chunks s for a launch of `items` CTA items (per chunk one CTA): the s
+// (1 <= s <= min(8, partners)) that fills the last wave of CTAs over the SMs best, the
+// smallest such s when several are within 1 %.
+static int pick_split(int items, int partners, int sms) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= std::min(8, partners); ++s) {
+    const long long ctas = (long long)items * s;
+    const long long waves = (ctas + sms - 1) / sms;
+    const double eff = (double)ctas / (double)(waves * sms);
+    if (eff > best_eff + 0.01) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+void choose_splits(tc_ctx* c) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  const Setup& S = c->S;
+  const int M = S.Nk * S.no, nj = S.Nk * S.nb;
+  for (int sides = 1; sides <= 2; ++sides) {
+    c->split_occ[sides - 1] = pick_split(M * sides, M, sms);
+    c->split_chain[sides - 1] = pick_split(nj * sides, M, sms);
+  }
+  c->so_max = std::max(c->split_occ[0], c->split_occ[1]);
+  c->sc_max = std::max(c->split_chain[0], c->split_chain[1]);
 }
 
 void ws_assign(tc_ctx* c, char* base, const WsLayout& L) {
@@ -356,6 +397,7 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
   c->esz = c->prec == TC_FP64 ? 16 : 8;
   c->ws_owned = own_workspace;
   cudaGetDevice(&c->device);
+  choose_splits(c);
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; return r == cudaSuccess; };
   const size_t nj = (size_t)S.Nk * S.nb;

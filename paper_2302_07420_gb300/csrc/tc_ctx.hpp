@@ -41,6 +41,10 @@ struct tc_ctx {
   double* d_cs = nullptr;          // [2][Nk*nb][no][6]
   void* d_scratch = nullptr;
   size_t scratch_bytes = 0;
+  // partner-chunk counts of k_occ_pairs / k_pair_chain for one-sided [0] and two-sided [1]
+  // launches (chosen from the SM count, see choose_splits) and the largest of each
+  int split_occ[2] = {1, 1}, split_chain[2] = {1, 1};
+  int so_max = 1, sc_max = 1;
   // workspace block holding d_phi .. d_scratch (owned unless the context belongs to a batch)
   void* d_ws = nullptr;
   bool ws_owned = true;
@@ -71,6 +75,10 @@ namespace tc {
 int init_context(const tc_params* p, bool own_workspace, tc_ctx** out, std::string& err);
 void destroy_context(tc_ctx* c);
 WsLayout ws_layout(const tc_ctx* c);
+// Chooses the partner-chunk counts of c for the current device (needs c->S).
+void choose_splits(tc_ctx* c);
+// n^3 volumes of one side's field block (see fill_side).
+size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max);
 void ws_assign(tc_ctx* c, char* base, const WsLayout& L);
 // Both operator sides into outR / outL (device pointers) on st, all terms of term_mask.
 int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st);
@@ -84,5 +92,5 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
                  const double* tw, int nsides, cudaStream_t st);
 template <typename T, int N> int prepare_kernels(tc_ctx* ctx);
 template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cudaStream_t st);
-template <typename T, int N> size_t scratch_needed(const Setup& S);
+template <typename T, int N> size_t scratch_needed(const Setup& S, int so_max, int sc_max);
 }  // namespace tc

@@ -26,13 +26,13 @@ template <typename T> struct SideArgs {
   cplx<T>* t3b2;         // [N]
   cplx<T>* vu;           // [2][N]   sum_{G != 0} u~_s(G) n~(G) e^{iG.r}  (no 1/Omega)
   cplx<T>* spec;         // [3][N]   spectral scratch
-  cplx<T>* h3a4;         // [Nk][no][3][N]
-  cplx<T>* h3b;          // [Nk][no][3][N]
+  cplx<T>* h3a4;         // [so][Nk][no][3][N]  one part per partner chunk (part 0 holds the sum)
+  cplx<T>* h3b;          // [so][Nk][no][3][N]
   cplx<T>* h5;           // [3][N]
   cplx<T>* h6;           // [N]
   cplx<T>* vloc;         // [N]
-  cplx<T>* acc;          // [Nk][nb][N]  output accumulator (real space)
-  cplx<T>* w;            // [Nk][nb][3][N]
+  cplx<T>* acc;          // [sc][Nk][nb][N]  output accumulator (real space), one part per partner chunk
+  cplx<T>* w;            // [sc][Nk][nb][3][N]
   cplx<T>* Z;            // [Nk][no][3][N]  -(s2b tw2bx1 grad ket_q + tw3a4 h3a4(q))
   cplx<T>* Y;            // [Nk][nb][3][N]  tw3b3 h1 ket_j - s2b tw2bx2 grad ket_j
   double* cs;            // [Nk*nb][no][6]: O_qj, X_pp, X_ap (re, im each): 3b6 correction scalars
@@ -44,6 +44,7 @@ template <typename T> struct SideArgs {
 template <typename T> struct Params {
   int Nk, nb, no, npw_max, ndelta;
   int nsmem;             // number of n^3 volumes held in shared memory
+  int so, sc;            // partner chunks per CTA item of k_occ_pairs / k_pair_chain (this launch)
   int div;
   T Bm[3][3];            // reciprocal rows b_i
   T invN;

@@ -246,9 +246,10 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
 }
 
 // ---------------------------------------------------------------------------
-// Occupied-pair stage.  Grid (Nk*no, 2 sides); CTA = occupied q2, loop over q1.
+// Occupied-pair stage.  Grid (Nk*no*so, 2 sides); CTA = occupied q2 and one of `so` chunks
+// of the q1 range (chunk parts of h3a4 / h3b, summed by k_sum_parts).
 //   P^s(a, b) = FT^{-1}[U^_s(k_b - k_a + G) FT[conj(bra_a) ket_b]],  U^_s = i p u~_s / Omega
-//   h6 += f1 f2 / Nk^2 sum_s P^s(q2,q1) . P^s(q1,q2)             (Alg. 4)
+//   h6 += f1 f2 / Nk^2 sum_s P^s(q2,q1) . P^s(q1,q2)             (Alg. 4; ap part over unordered pairs)
 //   h3a4(q2) += f1/Nk P^pp(q1,q2) ket_q1                         (Alg. 6)
 //   h3b(q2)  += f1/Nk P^pp(q2,q1) conj(bra_q1)                   (Algs. 8, 11)
 // Slots: 0 B1, 1 B2, 2 A1, 3 A2 (shared or global), 4 h6 part, 5 F_ab (global).
@@ -261,8 +262,11 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   __shared__ double sO[2][2];
   __shared__ double sF0[2];
   const SideArgs<T>& S = P.side[blockIdx.y];
-  const int k2 = blockIdx.x / P.no, mu2 = blockIdx.x % P.no;
+  const int M = P.Nk * P.no;                                   // occupied states
+  const int i2 = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
+  const int k2 = i2 / P.no, mu2 = i2 % P.no;
   const int q2 = k2 * P.nb + mu2;
+  const int i1_begin = (int)((long long)chunk * M / P.so), i1_end = (int)((long long)(chunk + 1) * M / P.so);
   cplx<T>* B1 = vol_slot<T, N>(P, sm, 0, NS);
   cplx<T>* B2 = vol_slot<T, N>(P, sm, 1, NS);
   cplx<T>* A1 = vol_slot<T, N>(P, sm, 2, NS);
@@ -271,8 +275,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   cplx<T>* FAB = vol_slot<T, N>(P, sm, 5, NS, true);
   const size_t NN = G::nn;
   const T f2 = (T)(P.occ[q2] / P.Nk);
-  cplx<T>* h3a4 = S.h3a4 + ((size_t)(k2 * P.no + mu2) * 3) * NN;
-  cplx<T>* h3b = S.h3b + ((size_t)(k2 * P.no + mu2) * 3) * NN;
+  cplx<T>* h3a4 = S.h3a4 + ((size_t)chunk * M + i2) * 3 * NN;
+  cplx<T>* h3b = S.h3b + ((size_t)chunk * M + i2) * 3 * NN;
   const cplx<T>* bra2 = S.bra + (size_t)q2 * NN;
   const cplx<T>* ket2 = S.ket + (size_t)q2 * NN;
   for (int r = threadIdx.x; r < G::vol; r += blockDim.x) FAB[r] = cplx<T>{0, 0};   // padded layout
@@ -285,12 +289,13 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   }
   if (threadIdx.x == 0) { sF0[0] = 0.0; sF0[1] = 0.0; }
   __syncthreads();
-  for (int k1 = 0; k1 < P.Nk; ++k1) {
+  for (int i1 = i1_begin; i1 < i1_end; ++i1) {
+    const int k1 = i1 / P.no, mu1 = i1 % P.no;
     const int id12 = P.delta_id[k2 * P.Nk + k1];   // Delta = k2 - k1 -> for P(q1,q2)
     const int id21 = P.delta_id[k1 * P.Nk + k2];   // Delta = k1 - k2 -> for P(q2,q1)
     const T* d12 = P.delta + id12 * 3;
     const T* d21 = P.delta + id21 * 3;
-    for (int mu1 = 0; mu1 < P.no; ++mu1) {
+    {
       const int q1 = k1 * P.nb + mu1;
       const T f1 = (T)(P.occ[q1] / P.Nk);
       if (f1 == T(0) || f2 == T(0)) continue;
@@ -317,7 +322,15 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
         for (int r = threadIdx.x; r < G::vol; r += blockDim.x) FAB[r] = FAB[r] + fq * (o12 * A1[r] + o21 * A2[r]);
         __syncthreads();
       }
+      // The antiparallel channel only feeds h6, and its contribution P^ap(q2,q1) . P^ap(q1,q2) is
+      // symmetric in (q1, q2): each unordered pair is taken once, by the CTA for which q1 lies
+      // in the next half of the cyclic order after q2, with weight 2 (1 on the diagonal).
+      const int cyc = (i1 - i2 + M) % M;
+      const bool ap_here = cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
+      const T ap_w = cyc == 0 ? T(1) : T(2);
       for (int sp = 0; sp < 2; ++sp) {
+        if (sp == 1 && !ap_here) continue;
+        const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
         for (int d = 0; d < 3; ++d) {
           const PComp<T> q21 = pcomp_setup<T>(P, d21, d), q12 = pcomp_setup<T>(P, d12, d);
           // B1 = P^s_d(q2, q1) (stored), B2 = P^s_d(q1, q2) (consumed with B1 in the last pass)
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
                 // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
                 const int g = G::gidx(i, j, k);
                 const cplx<T> b1 = B1[G::sidx(i, j, k)];
-                H6[g] = o.h6 + (f1 * f2) * (b1 * b2);
+                H6[g] = o.h6 + w12 * (b1 * b2);
                 if (sp == 0) {
                   h3a4[d * NN + g] = o.a + f1 * (b2 * ldg(ket1 + g));
                   h3b[d * NN + g] = o.b + f1 * mulc(b1, ldg(bra1 + g));
@@ -387,12 +400,14 @@ template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
   const int side = blockIdx.y;
   const SideArgs<T>& S = P.side[side];
   const size_t NN = G::nn;
-  const int ncta = P.Nk * P.no;
+  const int M = P.Nk * P.no, ncta = M * P.so;   // k_occ_pairs CTAs per side
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < (int)NN; r += gridDim.x * blockDim.x) {
     cplx<T> h6 = {0, 0}, h5[3] = {{0, 0}, {0, 0}, {0, 0}};
     for (int c = 0; c < ncta; ++c) {
       const size_t cta = (size_t)side * ncta + c;
       h6 = h6 + P.scratch[(cta * NS + 4) * (size_t)Geo<N>::vol + r];
+    }
+    for (int c = 0; c < M; ++c) {
       const int k = c / P.no, mu = c % P.no;
       const int q = k * P.nb + mu;
       const T f = (T)(P.occ[q] / P.Nk);
@@ -403,6 +418,25 @@ template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
     S.h6[r] = h6;
 #pragma unroll
     for (int d = 0; d < 3; ++d) S.h5[d * NN + r] = h5[d];
+  }
+}
+
+// Part 0 of a chunked accumulator += parts 1 .. nparts-1 (part = `len` elements), per side.
+// which: 0 h3a4 and h3b (k_occ_pairs), 1 acc and w (k_pair_chain).
+template <typename T, int N> __global__ void k_sum_parts(Params<T> P, int which) {
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const size_t NN = (size_t)N * N * N;
+  const size_t nj = (size_t)P.Nk * P.nb, M = (size_t)P.Nk * P.no;
+  const int nparts = which == 0 ? P.so : P.sc;
+  cplx<T>* a = which == 0 ? S.h3a4 : S.acc;
+  cplx<T>* b = which == 0 ? S.h3b : S.w;
+  const size_t la = which == 0 ? M * 3 * NN : nj * NN, lb = which == 0 ? M * 3 * NN : nj * 3 * NN;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < la + lb; e += (size_t)gridDim.x * blockDim.x) {
+    cplx<T>* base = e < la ? a + e : b + (e - la);
+    const size_t len = e < la ? la : lb;
+    cplx<T> v = base[0];
+    for (int c = 1; c < nparts; ++c) v = v + base[c * len];
+    base[0] = v;
   }
 }
 
@@ -445,7 +479,8 @@ template <typename T, int N> __global__ void k_prep_zy(Params<T> P) {
   }
 }
 
-// Fused pair chains, pass 1.  Grid (Nk*nb, 2 sides); CTA = output orbital j.
+// Fused pair chains, pass 1.  Grid (Nk*nb*sc, 2 sides); CTA = output orbital j and one of `sc`
+// chunks of the partner range (chunk parts of acc / w, summed by k_sum_parts).
 // For every occupied partner q (f = f_q / Nk, rho = conj(bra_q) ket_j):
 //   A  = FT[rho]
 //   2ax : acc -= tw f ket_q FT^{-1}[V(Delta + G) A]
@@ -468,15 +503,17 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   __shared__ T red[32];
   const SideArgs<T>& S = P.side[blockIdx.y];
-  const int j = blockIdx.x, kj = j / P.nb;
+  const int j = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
   cplx<T>* C = vol_slot<T, N>(P, sm, 1, NS);
   cplx<T>* A = vol_slot<T, N>(P, sm, 2, NS);
   const size_t NN = G::nn;
   const cplx<T>* ketj = S.ket + (size_t)j * NN;
   const cplx<T>* Yj = S.Y + (size_t)j * 3 * NN;
-  cplx<T>* acc = S.acc + (size_t)j * NN;
-  cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  cplx<T>* acc = S.acc + ((size_t)chunk * nj + j) * NN;
+  cplx<T>* w = S.w + ((size_t)chunk * nj + j) * 3 * NN;
   const T* tw = P.tw;
   const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
   const bool need_z = tw[T2BX1] != T(0) || tw[T3A4] != T(0);
@@ -490,13 +527,14 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
     for (int d = 0; d < 3; ++d) w[d * NN + r] = cplx<T>{0, 0};
   }
   __syncthreads();
-  for (int kq = 0; kq < P.Nk; ++kq) {
+  for (int qi = qi_begin; qi < qi_end; ++qi) {
+    const int kq = qi / P.no, mu = qi % P.no;
     const int did = P.delta_id[kj * P.Nk + kq];
     const T* dl = P.delta + did * 3;
     const T* Vt = S.tabV + ((size_t)did * 2 + S.side) * NN;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
     const T* Uap = P.tabU + ((size_t)did * 2 + 1) * NN;
-    for (int mu = 0; mu < P.no; ++mu) {
+    {
       const int q = kq * P.nb + mu;
       const T f = (T)(P.occ[q] / P.Nk);
       if (f == T(0)) continue;

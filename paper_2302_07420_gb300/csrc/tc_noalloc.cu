@@ -39,14 +39,6 @@ template <typename T> int prepare(tc_ctx* c, int n) {
   return TC_ERR_UNSUPPORTED;
 }
 
-template <typename T> size_t scratch_bytes(const tc::Setup& S, int n) {
-#define CASE(SLOT, NN) \
-  case NN: return tc::scratch_needed<T, NN>(S);
-  switch (n) { TC_FOR_N(CASE) }
-#undef CASE
-  return 0;
-}
-
 template <typename T>
 int run(tc_ctx* c, const double2* a, const double2* b, double2* oR, double2* oL, const double* tw, cudaStream_t st) {
 #define CASE(SLOT, NN) \
@@ -90,14 +82,15 @@ struct Carve {
 };
 
 struct Layout {
-  size_t box, kpg, did, delta, tabV, tabU, hartV, hartU, hartUs, occ, phi, chi, gphi, gchi, side, cs, scratch, total;
-  size_t side_bytes, scratch_len, cs_bytes;
+  size_t box, kpg, did, delta, tabV, tabU, hartV, hartU, hartUs, occ, ws, total;
+  tc::WsLayout W;   // the context's workspace block (fields, per-side fields, scratch) at offset ws
 };
 
-Layout plan(const tc::Setup& S, size_t esz, size_t rsz, size_t scratch_len) {
+Layout plan(const tc_ctx& ctx, size_t rsz) {
+  const tc::Setup& S = ctx.S;
   Layout L{};
   Carve c;
-  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb, vol = NN * esz;
+  const size_t nj = (size_t)S.Nk * S.nb;
   L.box = c.take(S.box_index.size() * sizeof(int));
   L.kpg = c.take((size_t)S.Nk * S.npw_max * 3 * sizeof(double));
   L.did = c.take(S.delta_id.size() * sizeof(int));
@@ -108,16 +101,8 @@ Layout plan(const tc::Setup& S, size_t esz, size_t rsz, size_t scratch_len) {
   L.hartU = c.take(S.hartU.size() * rsz);
   L.hartUs = c.take(S.hartUs.size() * rsz);
   L.occ = c.take(nj * sizeof(double));
-  L.phi = c.take(nj * vol);
-  L.chi = c.take(nj * vol);
-  L.gphi = c.take(nj * 3 * vol);
-  L.gchi = c.take(nj * 3 * vol);
-  L.side_bytes = (25 + (size_t)S.Nk * S.no * 9 + nj * 7) * vol;   // the per-side field block of tc_init
-  L.side = c.take(2 * L.side_bytes);
-  L.cs_bytes = (size_t)2 * nj * S.no * 6 * sizeof(double);
-  L.cs = c.take(L.cs_bytes);
-  L.scratch_len = scratch_len;
-  L.scratch = c.take(scratch_len);
+  L.W = tc::ws_layout(&ctx);
+  L.ws = c.take(L.W.total);
   L.total = (c.off + 255) & ~(size_t)255;
   return L;
 }
@@ -164,17 +149,23 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   const bool f64 = c.prec == TC_FP64;
   c.esz = f64 ? 16 : 8;
   const size_t rsz = f64 ? 8 : 4;
-  const Layout L = plan(S, c.esz, rsz, f64 ? scratch_bytes<double>(S, S.n) : scratch_bytes<float>(S, S.n));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  c.device = dev;
+  tc::choose_splits(&c);
+  Layout L = plan(c, rsz);
+  if (L.total > kNoallocBytes) {   // partner chunks multiply the accumulators: fall back to one chunk
+    c.split_occ[0] = c.split_occ[1] = c.split_chain[0] = c.split_chain[1] = 1;
+    c.so_max = c.sc_max = 1;
+    L = plan(c, rsz);
+  }
   if (L.total > kNoallocBytes)
     return fail(TC_ERR_UNSUPPORTED, "problem needs " + std::to_string(L.total) + " bytes of device scratch; the "
                                     "static arena holds " + std::to_string(kNoallocBytes) + " (TC_NOALLOC_MAX_BYTES)");
   for (const void* p : {phi_R, phi_L, (const void*)out_R, (const void*)out_L})
     if (p && !on_device(p)) return fail(TC_ERR_ARG, "orbital and output arrays must be device pointers");
 
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  c.device = dev;
   char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -207,8 +198,8 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   const size_t offs[] = {L.delta, L.tabV, L.tabU, L.hartV, L.hartU, L.hartUs};
   for (int i = 0; i < 6; ++i) ok(f64 ? put<double>(base + offs[i], *tabs[i], st) : put<float>(base + offs[i], *tabs[i], st));
   // the arena keeps the previous call's contents: start from the zeroed state of a fresh context
-  ok(cudaMemsetAsync(base + L.side, 0, 2 * L.side_bytes, st));
-  ok(cudaMemsetAsync(base + L.cs, 0, L.cs_bytes, st));
+  ok(cudaMemsetAsync(base + L.ws + L.W.side, 0, 2 * L.W.side_bytes, st));
+  ok(cudaMemsetAsync(base + L.ws + L.W.cs, 0, L.W.cs_bytes, st));
   if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
 
   c.d_box_index = reinterpret_cast<int*>(base + L.box);
@@ -221,15 +212,7 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   c.d_hartU = base + L.hartU;
   c.d_hartUs = base + L.hartUs;
   c.d_occ = reinterpret_cast<double*>(base + L.occ);
-  c.d_phi = base + L.phi;
-  c.d_chi = base + L.chi;
-  c.d_gphi = base + L.gphi;
-  c.d_gchi = base + L.gchi;
-  c.d_side = base + L.side;
-  c.side_bytes = L.side_bytes;
-  c.d_cs = reinterpret_cast<double*>(base + L.cs);
-  c.d_scratch = base + L.scratch;
-  c.scratch_bytes = L.scratch_len;
+  tc::ws_assign(&c, base + L.ws, L.W);
   double tw[TC_NTERMS_OP];
   const unsigned mask = S.prm.term_mask;
   for (int t = 0; t < TC_NTERMS_OP; ++t) tw[t] = (mask == 0u || ((mask >> t) & 1u)) ? 1.0 : 0.0;

@@ -10,10 +10,6 @@
 namespace tc {
 
 
-template <typename T> static inline size_t side_field_vols(int Nk, int nb, int no) {
-  // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc  = 25
-  return 25 + (size_t)Nk * no * 3 * 3 + (size_t)Nk * nb * (1 + 3 + 3);
-}
 
 template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideArgs<T>& s) {
   const size_t NN = (size_t)N * N * N;
@@ -24,10 +20,10 @@ template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideAr
   s.n = take(1); s.m = take(3); s.nt = take(1); s.mt = take(3); s.vH = take(1); s.h1 = take(3);
   s.vb2 = take(1); s.t3b1 = take(1); s.t3b2 = take(1); s.vu = take(2); s.spec = take(3); s.h5 = take(3);
   s.h6 = take(1); s.vloc = take(1);
-  s.h3a4 = take((size_t)S.Nk * S.no * 3);
-  s.h3b = take((size_t)S.Nk * S.no * 3);
-  s.acc = take((size_t)S.Nk * S.nb);
-  s.w = take((size_t)S.Nk * S.nb * 3);
+  s.h3a4 = take((size_t)ctx->so_max * S.Nk * S.no * 3);
+  s.h3b = take((size_t)ctx->so_max * S.Nk * S.no * 3);
+  s.acc = take((size_t)ctx->sc_max * S.Nk * S.nb);
+  s.w = take((size_t)ctx->sc_max * S.Nk * S.nb * 3);
   s.Z = take((size_t)S.Nk * S.no * 3);
   s.Y = take((size_t)S.Nk * S.nb * 3);
   s.cs = ctx->d_cs + (size_t)side * S.Nk * S.nb * S.no * 6;
@@ -123,10 +119,10 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
 // that are not in shared memory, and -- for boxes whose volume does not fit in
 // shared memory -- the work volume of every CTA of the single-volume kernels
 // (at most 8 per orbital in k_orbitals).  The uses never overlap in time.
-template <typename T, int N> size_t scratch_needed(const Setup& S) {
+template <typename T, int N> size_t scratch_needed(const Setup& S, int so_max, int sc_max) {
   const size_t vb = (size_t)vol_bytes<T, N>();
-  const size_t a = (size_t)2 * S.Nk * S.no * 6 * vb;
-  const size_t b = (size_t)2 * S.Nk * S.nb * 3 * vb;
+  const size_t a = (size_t)2 * S.Nk * S.no * so_max * 6 * vb;
+  const size_t b = (size_t)2 * S.Nk * S.nb * sc_max * 3 * vb;
   const size_t c = Fit<T, N>::one ? 0 : (size_t)8 * S.Nk * S.nb * vb;
   return std::max(a, std::max(b, c));
 }
@@ -168,6 +164,8 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   const int vb = vol_bytes<T, N>();
   const int vb1 = Fit<T, N>::one ? vb : 0;
   Params<T> P = make_params<T, N>(ctx, tw);
+  P.so = ctx->split_occ[nsides - 1];
+  P.sc = ctx->split_chain[nsides - 1];
   const int nj = S.Nk * S.nb;
   const int pw_blocks = 2 * 152;
   int nl[6] = {1, 9, 0, 1, 1, 1};   // kernel launches per stage
@@ -199,14 +197,19 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   if (need_a4) {
     Params<T> Pa = P;
     Pa.nsmem = smem_vols<T, N>(4);
-    k_occ_pairs<T, N><<<dim3(S.Nk * S.no, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
+    k_occ_pairs<T, N><<<dim3(S.Nk * S.no * P.so, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
     TC_CHECK_LAUNCH("k_occ_pairs");
+    if (P.so > 1) {
+      k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 0);
+      TC_CHECK_LAUNCH("k_sum_parts");
+      nl[2] += 1;
+    }
     k_reduce_a4<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(Pa);
     TC_CHECK_LAUNCH("k_reduce_a4");
     k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 3);
     k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 4);
     TC_CHECK_LAUNCH("hartree 3b2");
-    nl[2] = 4;
+    nl[2] += 4;
   }
   k_vloc<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_vloc");
@@ -218,9 +221,14 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   {
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);
-    k_pair_chain<T, N><<<dim3(nj, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
+    k_pair_chain<T, N><<<dim3(nj * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
     TC_CHECK_LAUNCH("k_pair_chain");
     stage_mark(ctx, st, 4);
+    if (P.sc > 1) {
+      k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 1);
+      TC_CHECK_LAUNCH("k_sum_parts");
+      nl[4] += 1;
+    }
     Params<T> Pb = P;
     Pb.nsmem = smem_vols<T, N>(2);
     k_pair_3b4<T, N><<<dim3(nj, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
@@ -253,6 +261,6 @@ template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cuda
                                   int, cudaStream_t);                                                     \
   template int prepare_kernels<T, N>(tc_ctx*);                                                           \
   template int run_fft3d<T, N>(void*, int, int, cudaStream_t);                                           \
-  template size_t scratch_needed<T, N>(const Setup&);
+  template size_t scratch_needed<T, N>(const Setup&, int, int);
 
 }  // namespace tc
