@@ -30,8 +30,22 @@ METRIC = "TC-operator orbital-pair convolutions/sec and % HBM roofline, FP32 vs 
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # derived ALU peak (FMA = 2 flop)
 FFTS_PER_PAIR_CHAIN = 15   # k_pair_chain: rho, V, 3 pp inverse, 3 pp forward, 3 ap inverse, 3 ap forward, final
+# DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload, from one 1-pass capture:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
+#       -k regex:k_pair_chain -s 3 -c 1 python bench.py --profile-run --steps 1 --warmup 3
+# (159.75 GB read + 77.19 GB written).  Reset to None whenever k_pair_chain changes.
+CHAIN_TRAFFIC_BYTES = 159.75e9 + 77.19e9
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
+
+
+def hbm_peak_gbps():
+    """Measured HBM copy bandwidth of this machine (MEASURED_PEAKS.json), else the stated fallback 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
 
 
 def pairs_per_apply(nk, nb, no):
@@ -122,6 +136,106 @@ def oracle_sample_pairs_per_s(nsteps=3, kmesh=(2, 2, 1)):
         "median of %d applies" % (kmesh + (npairs, nsteps)), "seconds": sum(times)}
 
 
+def measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev):
+    """Adjoint (FP32 tc_energy_grad on the same workload) and the 48^3 HEG (FP32 apply), device-timed."""
+    import torch
+    from paper_2302_07420_gb300 import synth
+    from paper_2302_07420_gb300.operator import Context
+    out = {}
+    ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                  precision="fp32")
+    ctx.energy_grad(d_phi, d_chi, occ)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.energy_grad(d_phi, d_chi, occ)
+    tg = time.perf_counter() - t0
+    nk, nb, no = ctx.nk, p["nbands"], p["nocc"]
+    ctx.close()
+    one_side = pairs_per_apply(nk, nb, no) // 2
+    out["adjoint"] = {"what": "tc_energy_grad: orbital gradients + dE/dA, dE/dC (pp, ap), FP32, same workload",
+                      "ms": 1e3 * tg, "passes": "1 two-sided apply + 8 one-sided energies",
+                      "pair_convolutions": 2 * one_side + 8 * one_side}
+    h = synth.WORKLOADS["heg_114"]()
+    hc = Context(h["lattice"], h["kmesh"], h["ecut"], h["fft"], h["nbands"], h["nocc"], h["A"], h["C"],
+                 precision="fp32")
+    npw, miller = hc.layout()
+    c = torch.from_numpy(synth.heg_orbitals(miller[0], hc.npw_max, 5)).to(dev)
+    hocc = synth.occupations(1, h["nbands"], h["nocc"])
+    r, l = hc.apply(c, c, hocc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        hc.apply(c, c, hocc, r, l)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 2
+    hc.close()
+    hp = pairs_per_apply(1, h["nbands"], h["nocc"])
+    out["heg_114_48"] = {"what": "HEG N=114 (57 plane waves), r_s=2, Gamma, 48^3 box, FP32 apply (R+L)",
+                         "ms_per_apply": ms, "pairs_per_apply": hp, "pairs_per_s": hp / (ms / 1e3)}
+    return out
+
+
+def run_batch(args):
+    """The 256-cell HEG batch (boxes 16^3-32^3, 1-8 k-points), FP32, one CUDA-graph launch per step."""
+    import torch
+    from paper_2302_07420_gb300 import synth
+    from paper_2302_07420_gb300.operator import BatchContext
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cells = synth.heg_batch(256)
+    bc = BatchContext(cells, precision="fp32")
+    dev = torch.device("cuda", local)
+    d, occ = [], []
+    for i, c in enumerate(cells):
+        nk, npw_max, npw, miller = bc.layouts[i]
+        kpg = kpg_list(c["lattice"], c["kmesh"], miller, npw)
+        d.append(torch.from_numpy(synth.heg_kpoint_orbitals(kpg, [miller[k, : npw[k]] for k in range(nk)], npw_max,
+                                                            c["nocc"])).to(dev))
+        occ.append(synth.occupations(nk, c["nbands"], c["nocc"]))
+    out_r = [torch.empty_like(x) for x in d]
+    out_l = [torch.empty_like(x) for x in d]
+    for _ in range(args.warmup):
+        bc.apply(d, d, occ, out_r, out_l)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bc.apply(d, d, occ, out_r, out_l)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    npairs = sum(pairs_per_apply(int(np.prod(c["kmesh"])), c["nbands"], c["nocc"]) for c in cells)
+    ncell, lanes, lanes_max, tune = bc.info()
+    bc.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": world * npairs * args.steps / t, "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "heg_batch: 256 HEG cells, N in {14,38,54,66}, r_s in [1,5], boxes 16^3-32^3, "
+                                   "1-8 k-points, plane-wave orbitals, one CUDA-graph launch per step",
+                       "pairs_per_step": npairs, "lanes": lanes, "lanes_max": lanes_max,
+                       "tune_ms_sample": {str(k): v for k, v in tune.items()},
+                       "l2": "no flush: the fields touched per step exceed the 129 MB L2"},
+            "clocks": clk.summary()}))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -156,14 +270,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="si_k444", choices=["si_k444", "si_k222"],
-                    help="si_k222 (2x2x2 mesh) is the small case used for ncu captures")
+    ap.add_argument("--workload", default="si_k444", choices=["si_k444", "si_k442", "si_k222", "heg_batch"],
+                    help="si_k442 / si_k222 (4x4x2 / 2x2x2 meshes) are smaller cases for ncu captures; heg_batch times the "
+                         "256-cell batch (one graph launch per step) and prints its own line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint and 48^3 timings added to the line")
     ap.add_argument("--profile-run", action="store_true",
                     help="FP32 applies only (warm-up + steps), no JSON line: the ncu capture command")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "heg_batch":
+        return run_batch(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -177,7 +296,8 @@ def main():
     from paper_2302_07420_gb300 import synth
     from paper_2302_07420_gb300.operator import Context
 
-    p = synth.WORKLOADS["si_k444"]() if args.workload == "si_k444" else synth.si_params(kmesh=(2, 2, 2))
+    p = (synth.WORKLOADS["si_k444"]() if args.workload == "si_k444"
+         else synth.si_params(kmesh=(4, 4, 2) if args.workload == "si_k442" else (2, 2, 2)))
     ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
                   precision="fp32")
     npw, miller = ctx.layout()
@@ -234,6 +354,13 @@ def main():
     flop_per_launch = chain_pairs * FFTS_PER_PAIR_CHAIN * fft_flop
     achieved = flop_per_launch / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e12
     launches = sum(v[1] for v in stages.values())
+    # HBM view of the same launch: measured DRAM bytes / live launch time, against the measured copy peak
+    traffic = CHAIN_TRAFFIC_BYTES if args.workload == "si_k444" else None
+    hbm = None
+    if traffic is not None:
+        gbps = traffic / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9
+        hbm = {"achieved": gbps, "peak": hbm_peak_gbps(), "unit": "GB/s", "frac": gbps / hbm_peak_gbps(),
+               "what": "ncu DRAM read+write bytes of one launch / its live CUDA-event time (of measured copy peak)"}
 
     # FP64 path (slow on GB300: low FP64 rate), same workload
     ctx64 = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
@@ -273,6 +400,10 @@ def main():
         te = float(tt.item())
     orb_bytes = c_phi.nbytes
 
+    extras = {}
+    if not args.no_extras and args.workload == "si_k444":
+        extras = measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, info = oracle_sample_pairs_per_s()
@@ -287,9 +418,10 @@ def main():
                        "l2": "no flush: the fields touched per step (~1 GB) exceed the 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "k_pair_chain",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_pair_chain",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                         "flop_per_launch": flop_per_launch, "ms_per_launch": pc_ms / max(pc_launch, 1)},
+                         "flop_per_launch": flop_per_launch, "ms_per_launch": pc_ms / max(pc_launch, 1),
+                         "hbm": hbm},
             "e2e": {"value": world * npairs * args.steps / te, "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * orb_bytes + occ.nbytes, "d2h_bytes_per_step": 2 * orb_bytes},
             "gpu_launches": launches,
@@ -300,6 +432,7 @@ def main():
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line))
     ctx.close()
     if dist is not None:

@@ -422,7 +422,7 @@ template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
 }
 
 // Part 0 of a chunked accumulator += parts 1 .. nparts-1 (part = `len` elements), per side.
-// which: 0 h3a4 and h3b (k_occ_pairs), 1 acc and w (k_pair_chain).
+// which: 0 h3a4 and h3b (k_occ_pairs), 1 acc and w (k_pair_chain), 2 acc only (k_pair_3b4).
 template <typename T, int N> __global__ void k_sum_parts(Params<T> P, int which) {
   const SideArgs<T>& S = P.side[blockIdx.y];
   const size_t NN = (size_t)N * N * N;
@@ -430,7 +430,7 @@ template <typename T, int N> __global__ void k_sum_parts(Params<T> P, int which)
   const int nparts = which == 0 ? P.so : P.sc;
   cplx<T>* a = which == 0 ? S.h3a4 : S.acc;
   cplx<T>* b = which == 0 ? S.h3b : S.w;
-  const size_t la = which == 0 ? M * 3 * NN : nj * NN, lb = which == 0 ? M * 3 * NN : nj * 3 * NN;
+  const size_t la = which == 0 ? M * 3 * NN : nj * NN, lb = which == 0 ? M * 3 * NN : (which == 1 ? nj * 3 * NN : 0);
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < la + lb; e += (size_t)gridDim.x * blockDim.x) {
     cplx<T>* base = e < la ? a + e : b + (e - la);
     const size_t len = e < la ? la : lb;
@@ -672,6 +672,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
 }
 
 // Pass 2 for 3b4 (Alg. 10): acc += tw f ket_q FT^{-1}[-U^pp . FT[-conj(bra_q) w_j]].
+// Grid (Nk*nb*sc, 2 sides): orbital j and one of `sc` chunks of the partner range.
 // Slots: 0 B (work), 1 A (spectral accumulator).
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
@@ -680,19 +681,27 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   const SideArgs<T>& S = P.side[blockIdx.y];
-  const int j = blockIdx.x, kj = j / P.nb;
+  const int j = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
   cplx<T>* A = vol_slot<T, N>(P, sm, 1, NS);
   const size_t NN = G::nn;
-  cplx<T>* acc = S.acc + (size_t)j * NN;
+  // chunk 0 adds to the complete accumulator (part 0); the others to their own zeroed parts
+  cplx<T>* acc = S.acc + ((size_t)chunk * nj + j) * NN;
   const cplx<T>* w = S.w + (size_t)j * 3 * NN;
   const T t3b4 = P.tw[T3B4];
   if (t3b4 == T(0)) return;
-  for (int kq = 0; kq < P.Nk; ++kq) {
+  if (chunk > 0) {
+    for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) acc[r] = cplx<T>{0, 0};
+    __syncthreads();
+  }
+  for (int qi = qi_begin; qi < qi_end; ++qi) {
+    const int kq = qi / P.no, mu = qi % P.no;
     const int did = P.delta_id[kj * P.Nk + kq];
     const T* dl = P.delta + did * 3;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
-    for (int mu = 0; mu < P.no; ++mu) {
+    {
       const int q = kq * P.nb + mu;
       const T f = (T)(P.occ[q] / P.Nk);
       if (f == T(0)) continue;

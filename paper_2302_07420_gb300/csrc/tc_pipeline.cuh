@@ -231,8 +231,13 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     }
     Params<T> Pb = P;
     Pb.nsmem = smem_vols<T, N>(2);
-    k_pair_3b4<T, N><<<dim3(nj, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
+    k_pair_3b4<T, N><<<dim3(nj * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
     TC_CHECK_LAUNCH("k_pair_3b4");
+    if (P.sc > 1 && tw[T3B4] != 0) {
+      k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 2);
+      TC_CHECK_LAUNCH("k_sum_parts");
+      nl[4] += 1;
+    }
   }
   // 5. local terms, corrections, back to the sphere
   stage_mark(ctx, st, 5);
