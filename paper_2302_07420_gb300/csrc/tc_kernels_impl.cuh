@@ -498,7 +498,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) {
   using G = Geo<N>;
   constexpr int NS = 3;
-  constexpr int CH = 8;
+  constexpr int CH = 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   __shared__ T red[32];
@@ -616,18 +616,26 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
                   if (need_z) oa[u] = acc[g];
                   if (need_w) ow[u] = w[d * NN + g];
                 }
+                cplx<T> lz[CH], lk[CH], ly[CH], lb[CH], lj[CH], lh[CH], ln[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                  if (c0 + u >= N) continue;
+                  const int g = G::gidx(c0 + u, i2, i3);
+                  lz[u] = ldg(Zq + d * NN + g); lk[u] = ldg(ketq + g); ly[u] = ldg(Yj + d * NN + g);
+                  lb[u] = ldg(braq + g); lj[u] = ldg(ketj + g); lh[u] = ldg(h3bq + d * NN + g); ln[u] = ldg(S.n + g);
+                }
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
                   if (c0 + u >= N) continue;
                   const int g = G::gidx(c0 + u, i2, i3);
                   const cplx<T> bv = v[c0 + u];
-                  if (need_z) acc[g] = oa[u] + f * (ldg(Zq + d * NN + g) * bv);
-                  if (need_w) w[d * NN + g] = ow[u] + f * (ldg(ketq + g) * bv);
+                  if (need_z) acc[g] = oa[u] + f * (lz[u] * bv);
+                  if (need_w) w[d * NN + g] = ow[u] + f * (lk[u] * bv);
                   cplx<T> F = {0, 0};
                   if (need_F) {
-                    if (need_y) F = mulc(ldg(Yj + d * NN + g), ldg(braq + g));
-                    if (t3b5 != T(0)) F = F - t3b5 * (ldg(ketj + g) * ldg(h3bq + d * NN + g));
-                    if (t3b6 != T(0)) F = F + t3b6 * (ldg(S.n + g) * bv);
+                    if (need_y) F = mulc(ly[u], lb[u]);
+                    if (t3b5 != T(0)) F = F - t3b5 * (lj[u] * lh[u]);
+                    if (t3b6 != T(0)) F = F + t3b6 * (ln[u] * bv);
                   }
                   v[c0 + u] = F;
                 }
