@@ -239,6 +239,58 @@ __device__ __forceinline__ void inv3d(cplx<T>* W, Load load, Emit emit) {
   fft_pass<T, N, +1, 1>([&](int a, int b, int c) { return W[G::sidx(a, b, c)]; }, emit);
 }
 
+// A pass whose store needs per-element data from global memory: after the
+// transform of a pencil, pre(i1, i2, i3) is evaluated for a chunk of CH
+// elements before store(i1, i2, i3, v, pre_value) runs on any of them, so the
+// loads of a chunk are in flight together (each store through a generic
+// pointer would otherwise hold back every later load).
+template <typename T, int N, int S, int AXIS, int CH, typename Load, typename Pre, typename Store>
+__device__ __forceinline__ void fft_pass_pre(Load load, Pre pre, Store store) {
+  for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+    const int a = p / N, b = p % N;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      if (AXIS == 1) v[i] = load(i, a, b);
+      else if (AXIS == 2) v[i] = load(a, i, b);
+      else v[i] = load(a, b, i);
+    }
+    Codelet<T, N, S>::run(v);
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += CH) {
+      decltype(pre(0, 0, 0)) o[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int i = c0 + u;
+        if (i >= N) continue;
+        if (AXIS == 1) o[u] = pre(i, a, b);
+        else if (AXIS == 2) o[u] = pre(a, i, b);
+        else o[u] = pre(a, b, i);
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int i = c0 + u;
+        if (i >= N) continue;
+        if (AXIS == 1) store(i, a, b, v[i], o[u]);
+        else if (AXIS == 2) store(a, i, b, v[i], o[u]);
+        else store(a, b, i, v[i], o[u]);
+      }
+    }
+  }
+}
+
+// Forward transform whose emit needs per-element global data (see fft_pass_pre).
+template <typename T, int N, int CH, typename Load, typename Pre, typename Emit>
+__device__ __forceinline__ void fwd3d_pre(cplx<T>* W, Load load, Pre pre, Emit emit) {
+  using G = Geo<N>;
+  fft_pass<T, N, -1, 1>(load, [&](int a, int b, int c, cplx<T> v) { W[G::sidx(a, b, c)] = v; });
+  __syncthreads();
+  fft_pass<T, N, -1, 3>([&](int a, int b, int c) { return W[G::sidx(a, b, c)]; },
+                        [&](int a, int b, int c, cplx<T> v) { W[G::sidx(a, b, c)] = v; });
+  __syncthreads();
+  fft_pass_pre<T, N, -1, 2, CH>([&](int a, int b, int c) { return W[G::sidx(a, b, c)]; }, pre, emit);
+}
+
 // Last (axis-1) pass of an inverse transform that feeds a read-modify-write of
 // global arrays.  Per pencil and chunk of CH elements, pre(i1, i2, i3) loads
 // every old value first and post(i1, i2, i3, v, old) then computes and stores,

@@ -87,6 +87,11 @@ template <typename T, int N> __device__ __forceinline__ T pcomp(const PComp<T>& 
 
 template <typename T> __device__ __forceinline__ cplx<T> ld(const cplx<T>* p, size_t i) { return p[i]; }
 
+// Old accumulator value and partner ket of one element, loaded together before a store.
+template <typename T> struct AccKet {
+  cplx<T> acc, ket;
+};
+
 template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -573,10 +578,12 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
         const T fw = -f * tw[T2AX];
         inv3d_rmw<T, N, CH>(
             B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
-            [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
-            [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+            [&](int a, int b, int c) {
               const int g = G::gidx(a, b, c);
-              acc[g] = o + fw * (ldg(ketq + g) * v);
+              return AccKet<T>{acc[g], ldg(ketq + g)};
+            },
+            [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
+              acc[G::gidx(a, b, c)] = o.acc + fw * (o.ket * v);
             });
         __syncthreads();
       }
@@ -654,24 +661,27 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
           fft_pass<T, N, -1, 3>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
                                 [&](int a, int b, int c, cplx<T> v) { B[G::sidx(a, b, c)] = v; });
           __syncthreads();
-          fft_pass<T, N, -1, 2>([&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
-                                [&](int a, int b, int c, cplx<T> v) {
-                                  // -U_d FT[F] = -i p_d u (v / N)
-                                  const cplx<T> t =
-                                      mul_si<T, -1>((pcomp<T, N>(qd, a, b, c) * Ut[G::gidx(a, b, c)] * P.invN) * v);
-                                  const int s = G::sidx(a, b, c);
-                                  C[s] = first_C ? t : C[s] + t;
-                                });
+          fft_pass_pre<T, N, -1, 2, 8>(
+              [&](int a, int b, int c) { return B[G::sidx(a, b, c)]; },
+              [&](int a, int b, int c) { return pcomp<T, N>(qd, a, b, c) * Ut[G::gidx(a, b, c)] * P.invN; },
+              [&](int a, int b, int c, cplx<T> v, T k) {
+                // -U_d FT[F] = -i p_d u (v / N)
+                const cplx<T> t = mul_si<T, -1>(k * v);
+                const int s = G::sidx(a, b, c);
+                C[s] = first_C ? t : C[s] + t;
+              });
           __syncthreads();
         }
       }
       if (need_F || need_ap) {
         inv3d_rmw<T, N, CH>(
             B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
-            [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
-            [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+            [&](int a, int b, int c) {
               const int g = G::gidx(a, b, c);
-              acc[g] = o + f * (ldg(ketq + g) * v);
+              return AccKet<T>{acc[g], ldg(ketq + g)};
+            },
+            [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
+              acc[G::gidx(a, b, c)] = o.acc + f * (o.ket * v);
             });
         __syncthreads();
       }
@@ -717,11 +727,12 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
       const cplx<T>* ketq = S.ket + (size_t)q * NN;
       for (int d = 0; d < 3; ++d) {
         const PComp<T> qd = pcomp_setup<T>(P, dl, d);
-        fwd3d<T, N>(
+        fwd3d_pre<T, N, 8>(
             B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(w + d * NN + g), ldg(braq + g)); },
-            [&](int a, int b, int c, cplx<T> v) {
+            [&](int a, int b, int c) { return pcomp<T, N>(qd, a, b, c) * Upp[G::gidx(a, b, c)] * P.invN; },
+            [&](int a, int b, int c, cplx<T> v, T k) {
               // -U_d FT[-conj(bra_q) w_d] = +i p_d u FT[conj(bra_q) w_d]
-              const cplx<T> t = mul_si<T, 1>((pcomp<T, N>(qd, a, b, c) * Upp[G::gidx(a, b, c)] * P.invN) * v);
+              const cplx<T> t = mul_si<T, 1>(k * v);
               const int s = G::sidx(a, b, c);
               A[s] = d == 0 ? t : A[s] + t;
             });
@@ -730,10 +741,12 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
       const T fw = t3b4 * f;
       inv3d_rmw<T, N, 8>(
           B, [&](int a, int b, int c) { return A[G::sidx(a, b, c)]; },
-          [&](int a, int b, int c) { return acc[G::gidx(a, b, c)]; },
-          [&](int a, int b, int c, cplx<T> v, cplx<T> o) {
+          [&](int a, int b, int c) {
             const int g = G::gidx(a, b, c);
-            acc[g] = o + fw * (ldg(ketq + g) * v);
+            return AccKet<T>{acc[g], ldg(ketq + g)};
+          },
+          [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
+            acc[G::gidx(a, b, c)] = o.acc + fw * (o.ket * v);
           });
       __syncthreads();
     }
