@@ -346,8 +346,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
                 return mul_si<T, 1>((pcomp<T, N>(q21, i, j, k) * u) * A1[G::sidx(i, j, k)]);
               },
               [&](int i, int j, int k, cplx<T> v) { B1[G::sidx(i, j, k)] = v; });
-          struct Old3 { cplx<T> h6, a, b; };
-          inv3d_rmw<T, N, 8>(
+          // old accumulator values, B1 and the partner fields of one element, loaded before any store
+          struct Old3 { cplx<T> h6, a, b, b1, k1, br1; };
+          inv3d_rmw<T, N, 4>(
               B2,
               [&](int i, int j, int k) {
                 const T u = P.tabU[((size_t)id12 * 2 + sp) * NN + G::gidx(i, j, k)];
@@ -357,20 +358,22 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
                 const int g = G::gidx(i, j, k);
                 Old3 o;
                 o.h6 = H6[g];
+                // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
+                o.b1 = B1[G::sidx(i, j, k)];
                 if (sp == 0) {
                   o.a = h3a4[d * NN + g];
                   o.b = h3b[d * NN + g];
+                  o.k1 = ldg(ket1 + g);
+                  o.br1 = ldg(bra1 + g);
                 }
                 return o;
               },
               [&](int i, int j, int k, cplx<T> b2, const Old3& o) {
-                // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
                 const int g = G::gidx(i, j, k);
-                const cplx<T> b1 = B1[G::sidx(i, j, k)];
-                H6[g] = o.h6 + w12 * (b1 * b2);
+                H6[g] = o.h6 + w12 * (o.b1 * b2);
                 if (sp == 0) {
-                  h3a4[d * NN + g] = o.a + f1 * (b2 * ldg(ket1 + g));
-                  h3b[d * NN + g] = o.b + f1 * mulc(b1, ldg(bra1 + g));
+                  h3a4[d * NN + g] = o.a + f1 * (b2 * o.k1);
+                  h3b[d * NN + g] = o.b + f1 * mulc(o.b1, o.br1);
                 }
               });
           __syncthreads();
