@@ -6,7 +6,7 @@
  * V3body; the three-body part contracted over occupied orbitals as in
  * Eq. SCF / Eq. BITCSCF) to every right orbital phi and every left orbital chi
  * at every k-point, including the divergence corrections for k-points on the
- * SCF mesh (Sec. 2.6 and the corrections listed in Sec. 2.7.4).  One spin
+ * SCF mesh (Sec. 2.5 and the corrections listed in Sec. 2.6.4).  One spin
  * channel is computed (non-spin-polarised: both channels hold the same
  * orbitals); same-spin pairs use the parallel-spin Jastrow (A[0], C[0]) and
  * opposite-spin pairs the antiparallel one (A[1], C[1]).
@@ -14,7 +14,7 @@
  * Units: Hartree atomic units.  Orbitals are given by their plane-wave
  * coefficients c(G) on the sphere |k+G|^2/2 <= ecut_ha, normalised so that
  * sum_G |c(G)|^2 = 1 (phi_periodic(r) = sum_G c(G) e^{iG.r} / sqrt(Omega),
- * Sec. 2.4).  Outputs are coefficients in the same units on the same sphere.
+ * Sec. 2.3).  Outputs are coefficients in the same units on the same sphere.
  *
  * Layout of every orbital array: interleaved complex FP64
  * [Nk][nbands][npw_max] (real, imaginary), zero padded beyond npw(k), in the
@@ -57,7 +57,7 @@ typedef enum {
 
 enum { TC_FP64 = 0, TC_FP32 = 1 };
 
-/* Term indices of the operator (Sec. 2.7.3-2.7.4) and of E_terms.  The
+/* Term indices of the operator (Sec. 2.6.3-2.6.4) and of E_terms.  The
  * three-body outputs include their multiplicities: 3a3 and 3a4 twice (3a6 = 3a3,
  * 3a5 = 3a4), every 3b term twice (3c = 3b). */
 enum {

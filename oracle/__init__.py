@@ -10,9 +10,9 @@ What it computes (M. Ochi, "TC++: First-principles calculation code for solids
 using the transcorrelated method", arXiv:2302.07420):
 
 * ``cell``      -- cell, Gamma-centred k mesh, plane-wave spheres, FFT box,
-                   Gygi-Baldereschi constant (Sec. 2.6, Eqs. correction2, aux).
+                   Gygi-Baldereschi constant (Sec. 2.5, Eqs. correction2, aux).
 * ``kernels``   -- Fourier transforms of u, lap u, (grad u)^2 and V_2a
-                   (Sec. 2.7.3 and Appendix B).
+                   (Sec. 2.6.3 and Appendix B).
 * ``operator``  -- the two-body terms 2ah, 2bh1, 2bh2, 2ax, 2bx1, 2bx2 and the
                    three-body terms 3a1-3a4, 3b1-3b6 (Algorithms 1-12), with the
                    divergence corrections for k on the SCF mesh

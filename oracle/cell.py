@@ -16,7 +16,7 @@ Conventions (arXiv:2302.07420):
 * periodic Fourier transform with the 1/Omega convention of Sec. 2.2, which on
   the grid is FT[f](G) = (1/N) sum_r f(r) e^{-iG.r}, FT^{-1}[F](r) = sum_G F(G) e^{iG.r}.
 
-Divergence correction (Sec. 2.6): with the auxiliary function
+Divergence correction (Sec. 2.5): with the auxiliary function
 A_aux(q) = exp(-alpha q^2)/q^2 (Eq. aux) and k on the SCF mesh, the bracket of
 Eq. correction2 is
 

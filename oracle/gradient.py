@@ -32,7 +32,7 @@ kernel data K.  Hence along the derivative direction dK = dK/dtheta,
     dE/dtheta = [E(K + t dK) - E(K - t dK)] / (2 t)
 holds for any t without truncation error.  dK comes from
 ``kernels.JastrowKernels(deriv=...)`` (closed-form derivatives of the
-transforms of Sec. 2.7.3 and Appendix B).
+transforms of Sec. 2.6.3 and Appendix B).
 
 Parity pins (tests/test_oracle_gradient.py): the orbital gradient against an
 exact 4-point stencil of E along random directions, corrections on and off;

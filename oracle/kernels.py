@@ -5,11 +5,11 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Jastrow function u(r) = A/r (1 - exp(-r/C)) (Eq. Jastrow).  Non-periodic Fourier
 transforms (Sec. 2.2 convention, g~(G) = int dr g(r) e^{-iG.r}):
 
-* u~(p)          = 4 pi A (1/p^2 - 1/(p^2 + C^-2))      (Sec. 2.7.3)
+* u~(p)          = 4 pi A (1/p^2 - 1/(p^2 + C^-2))      (Sec. 2.6.3)
 * (lap u)~(p)    = -p^2 u~(p) = -4 pi A C^-2/(p^2 + C^-2)
 * ((grad u)^2)~  = (4 pi A^2/(C g)) B(g), g = C p, with
   B(g) = -(pi/4) g^2 - (1 + g^2/2) atan(g/2) + (1 + g^2) atan(g)   (Eq. fourier_transform_nabla2u, App. B)
-* V_2a(p)        = 4 pi/p^2 + (lap u)~ - ((grad u)^2)~   (Sec. 2.7.3: 1/r + (1/2)[lap1 u + lap2 u
+* V_2a(p)        = 4 pi/p^2 + (lap u)~ - ((grad u)^2)~   (Sec. 2.6.3: 1/r + (1/2)[lap1 u + lap2 u
                    - (grad1 u)^2 - (grad2 u)^2], both Laplacians and both squared
                    gradients being the same function of r1 - r2)
 * V_2a^dagger(p) = 4 pi/p^2 - (lap u)~ - ((grad u)^2)~  (the 1/r + ... part of v_2body^dagger:
@@ -104,7 +104,7 @@ def V2a(p2, A, C, adjoint=False):
 def V2a_jastrow_zero(A, C):
     """Finite Jastrow part of V_2a at p = 0: (lap u)~(0) - ((grad u)^2)~(0).
 
-    The Coulomb 4 pi/p^2 part is the only divergent piece (Sec. 2.7.3, after
+    The Coulomb 4 pi/p^2 part is the only divergent piece (Sec. 2.6.3, after
     Eq. divcorr_2ax_scf); it is dropped at p = 0 and replaced by the divergence
     correction.  The same value is used for V_2a^dagger: on the grid the
     grad u . grad terms vanish at p = 0 (their kernel i p u~ is set to zero there), so the

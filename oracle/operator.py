@@ -2,14 +2,14 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Follows Sec. 2.7 of arXiv:2302.07420 step by step.  One spin channel is
+Follows Sec. 2.6 of arXiv:2302.07420 step by step.  One spin channel is
 computed (non-spin-polarised, the two spin channels hold identical orbitals):
 exchange-type terms pair same-spin orbitals only and use the parallel-spin
 Jastrow (A_pp, C_pp); Hartree-type sums and the sums over a free spin index in
 3a2 and 3b6 take both channels, i.e. pp + ap kernels.
 
 Units.  An orbital is held as psi(r) = sum_G c(G) e^{iG.r} = sqrt(Omega)
-phi_periodic(r) (the dimensionless array of Sec. 2.7.1), with sum |c|^2 = 1.
+phi_periodic(r) (the dimensionless array of Sec. 2.6.1), with sum |c|^2 = 1.
 Every kernel K of the paper then enters divided by Omega (K^ = K/Omega), the
 density is n_psi = (1/N_k) sum_q f_q chi_q^* phi_q in the same units, and the
 output coefficients are those of g_j in the units of c.
@@ -19,12 +19,12 @@ rho_qj = chi_q^* phi_j, Delta = k - q, U^_s(p) = i p u~_s(p)/Omega (zero at p = 
 and P^s(a, b) = FT^{-1}[U^_s(k_b - k_a + G) FT[chi_a^* phi_b]]:
 
   2ah   Alg. 1        v_H phi_j,          v_H = FT^{-1}[(V^pp + V^ap)^ n~]  (G != 0)
-  2bh1  Sec. 2.7.3    h1 . grad phi_j,    h1 = FT^{-1}[i G (u~pp + u~ap)^ n~]
-  2bh2  Sec. 2.7.3    v_b2 phi_j,         v_b2 = FT^{-1}[-i G (u~pp + u~ap)^ . m~],
+  2bh1  Sec. 2.6.3    h1 . grad phi_j,    h1 = FT^{-1}[i G (u~pp + u~ap)^ n~]
+  2bh2  Sec. 2.6.3    v_b2 phi_j,         v_b2 = FT^{-1}[-i G (u~pp + u~ap)^ . m~],
                                           m = (1/N_k) sum_q f_q chi_q^* grad phi_q
   2ax   Alg. 2        -sum_q f_q/N_k phi_q FT^{-1}[V^pp(Delta + G) rho~_qj]
-  2bx1  Sec. 2.7.3    -sum_q f_q/N_k grad phi_q . FT^{-1}[U^pp rho~_qj]
-  2bx2  Sec. 2.7.3    +sum_q f_q/N_k phi_q FT^{-1}[U^pp . FT[chi_q^* grad phi_j]]
+  2bx1  Sec. 2.6.3    -sum_q f_q/N_k grad phi_q . FT^{-1}[U^pp rho~_qj]
+  2bx2  Sec. 2.6.3    +sum_q f_q/N_k phi_q FT^{-1}[U^pp . FT[chi_q^* grad phi_j]]
   3a1   Alg. 3        -(1/2) (h1 . h1) phi_j
   3a2   Alg. 4        (1/2) h6 phi_j,     h6 = sum_{q1,q2} f f/N_k^2 sum_s P^s(q2,q1) . P^s(q1,q2)
   3a3   Alg. 5        (1/2) h1 . w_j,     w_j = sum_q f_q/N_k phi_q FT^{-1}[U^pp rho~_qj]
@@ -40,7 +40,7 @@ and P^s(a, b) = FT^{-1}[U^_s(k_b - k_a + G) FT[chi_a^* phi_b]]:
   3b5   Alg. 11       -(1/2) sum_q2 f/N_k phi_q2 FT^{-1}[-U^pp . FT[phi_j h3b(q2)]]
   3b6   Alg. 12       (1/2) sum_q2 f/N_k phi_q2 FT^{-1}[sum_s -U^s . FT[n FT^{-1}[U^s rho~_q2j]]]
 
-Multiplicities (Sec. 2.7.4): the full three-body operator is
+Multiplicities (Sec. 2.6.4): the full three-body operator is
 3a1 + 3a2 + 2*3a3 + 2*3a4 + 2*(3b1 + ... + 3b6) because 3a5 = 3a4, 3a6 = 3a3 and
 3c* = 3b*; the outputs below carry these factors.  The printed |h1|^2 of
 Algorithm 3 is read as h1 . h1 (no conjugate): the integrand has two bra
@@ -62,7 +62,7 @@ Gamma0 = Omega/(4 sqrt(pi^3 alpha)) - (1/N_k)(-alpha + sum' A_aux) (Eq. correcti
         + (4 pi A/N_k)/Omega^2 sum_{G != 0} u~(G) (F_a(G) + F_b(G)) e^{iG.r}, x = ushort_factor.
   3b6   Eqs. 3b6_div_scf1/2/3 (times the multiplicity 2).
 The grad-u (odd) corrections of 2bx1, 2bx2, 3a3, 3a4, 3b3, 3b4, 3b5 vanish for
-k on the uniform SCF mesh (Sec. 2.6, Eq. correction_nabla) and are not added.
+k on the uniform SCF mesh (Sec. 2.5, Eq. correction_nabla) and are not added.
 
 Energy (Eqs. EtotTC / EtotBiTC, single determinant): per unit cell, both spins,
 E = (2/N_k) Re sum_{k,mu} f [<chi|T|phi> + (1/2) <chi|g_2> + (1/3) <chi|g_3>].
@@ -364,7 +364,7 @@ def tc_apply(S, c_phi, c_chi, occ, kpoints=None, backend=None):
 
 
 def kinetic_coeffs(S, c):
-    """T c = |k+G|^2/2 c on every sphere (Sec. 2.7.2)."""
+    """T c = |k+G|^2/2 c on every sphere (Sec. 2.6.2)."""
     out = np.zeros_like(c)
     for k in range(S.Nk):
         kg = S.kpG(k)

@@ -1,6 +1,6 @@
 // Kernels of the TC operator (templated on precision T and cubic box size N).
 //
-// Stage map (Sec. 2.7 of arXiv:2302.07420):
+// Stage map (Sec. 2.6 of arXiv:2302.07420):
 //   k_orbitals     sphere -> box gather and inverse FFT of phi, chi, grad phi, grad chi
 //   k_density      n and the 2bh2 vector density m (per side)
 //   k_spec_fwd     FT of a global field or of a product of two fields

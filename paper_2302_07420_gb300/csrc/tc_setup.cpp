@@ -17,7 +17,7 @@ namespace tc {
 static const double kPi = 3.14159265358979323846;
 static const double k4Pi = 4.0 * kPi;
 
-// --- Jastrow kernel transforms (Sec. 2.7.3, Appendix B) -----------------------
+// --- Jastrow kernel transforms (Sec. 2.6.3, Appendix B) -----------------------
 // u~(p) = 4 pi A (1/p^2 - 1/(p^2 + C^-2)) in the cancellation-free form.
 double host_u_tilde(double p2, double A, double C) {
   const double c2 = 1.0 / (C * C);

@@ -1,4 +1,4 @@
-"""Pins of the oracle's basis and divergence-correction constant (Sec. 2.6)."""
+"""Pins of the oracle's basis and divergence-correction constant (Sec. 2.5)."""
 import numpy as np
 import pytest
 

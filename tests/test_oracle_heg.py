@@ -3,7 +3,7 @@
 For plane-wave orbitals psi_n = e^{iG_n.r} (Gamma only, chi = phi, f = 1) every
 term of the operator is diagonal in momentum and its eigenvalue is a finite
 lattice sum over the occupied set O, derived by hand from the algorithms
-(Sec. 2.7) -- no FFT and no grid.  With D = G_n - G_m, U(D) = i D u~pp(D)/Omega,
+(Sec. 2.6) -- no FFT and no grid.  With D = G_n - G_m, U(D) = i D u~pp(D)/Omega,
 a(q) = sum_{m in O, m != q} U(G_q - G_m), c_s = (4 pi A_s)^2 Gamma0
 + x 4 pi A_s u_short,s (N_k = 1):
 

@@ -146,3 +146,25 @@ def test_pins_detect_a_planted_mistake(term, monkeypatch):
     rhs = np.conj(out_l[0]) @ c_phi[0].T
     adj_broken = np.abs(lhs - rhs).max() > 1e-10 * np.abs(lhs).max()
     assert grad_broken or adj_broken
+
+
+def test_partners_enter_only_through_the_density_matrix():
+    """Density-matrix mixing (Sec. 2.4): partners enter the operator only through sum_q f_q phi_q chi_q^*.
+
+    Splitting every partner into two identical copies with occupations beta f and (1 - beta) f
+    leaves every output unchanged, divergence corrections (general-overlap forms) included.
+    """
+    p = synth.tiny_params(3, kmesh=(1, 1, 2), fft=(9, 9, 11), ecut=1.6, nbands=2, nocc=2, scale=5.0)
+    S1 = make_setup(p)
+    c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 77, [S1.kpG(k) for k in range(S1.Nk)], S1.npw_max, 2,
+                                         perturb=0.1)
+    occ1 = np.array([[1.0, 0.6]] * S1.Nk)
+    r1, l1 = OP.tc_apply(S1, c_phi, c_chi, occ1)
+    S2 = make_setup(p, nbands=4, nocc=4)
+    beta = 0.3
+    r2, l2 = OP.tc_apply(S2, np.concatenate([c_phi, c_phi], axis=1), np.concatenate([c_chi, c_chi], axis=1),
+                         np.concatenate([beta * occ1, (1 - beta) * occ1], axis=1))
+    scale = np.abs(r1).max()
+    for half in (slice(0, 2), slice(2, 4)):
+        np.testing.assert_allclose(r2[:, half], r1, rtol=0, atol=1e-13 * scale)
+        np.testing.assert_allclose(l2[:, half], l1, rtol=0, atol=1e-13 * scale)

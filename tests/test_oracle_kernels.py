@@ -1,4 +1,4 @@
-"""Pins of the oracle's kernel transforms against quadrature and limits (Sec. 2.7.3, App. B)."""
+"""Pins of the oracle's kernel transforms against quadrature and limits (Sec. 2.6.3, App. B)."""
 import numpy as np
 import pytest
 from scipy import integrate, special
