@@ -155,6 +155,22 @@ def measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev):
     out["adjoint"] = {"what": "tc_energy_grad: orbital gradients + dE/dA, dE/dC (pp, ap), FP32, same workload",
                       "ms": 1e3 * tg, "passes": "1 two-sided apply + 8 one-sided energies",
                       "pair_convolutions": 2 * one_side + 8 * one_side}
+    # one block-Davidson step on the same cell (FP32 operator launches, FP64 subspace work)
+    ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                  precision="fp32")
+    ctx.davidson_step(d_phi, d_chi, occ)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nd = 2
+    for _ in range(nd):
+        _, _, eig, dim = ctx.davidson_step(d_phi, d_chi, occ)
+    td = (time.perf_counter() - t0) / nd
+    ctx.close()
+    out["davidson_step"] = {"what": "tc_davidson_step: h v, Payne + Gram-Schmidt, h w, FP64 subspace eigenpairs, "
+                                    "Ritz vectors + biorthonormalisation (host-synchronous call, wall time)",
+                            "ms": 1e3 * td, "subspace_dim": [int(dim.min()), int(dim.max())],
+                            "pair_chains": one_side + (nk * (no + nb)) * (nk * no),
+                            "lowest_ritz_value_k0": float(eig[0, 0].real)}
     h = synth.WORKLOADS["heg_114"]()
     hc = Context(h["lattice"], h["kmesh"], h["ecut"], h["fft"], h["nbands"], h["nocc"], h["A"], h["C"],
                  precision="fp32")

@@ -52,7 +52,9 @@ typedef enum {
   TC_ERR_OOM = 3,          /* device or host allocation failed (tc_init only) */
   TC_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
   TC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
-  TC_ERR_UNSUPPORTED = 6   /* valid but not supported (e.g. FFT box size) */
+  TC_ERR_UNSUPPORTED = 6,  /* valid but not supported (e.g. FFT box size) */
+  TC_ERR_NUMERIC = 7       /* a numerical step failed (vanishing norm, singular overlap,
+                              eigen-solver without convergence); outputs undefined */
 } tc_status;
 
 enum { TC_FP64 = 0, TC_FP32 = 1 };
@@ -147,6 +149,39 @@ tc_status tc_energy_grad(tc_ctx* ctx, const void* phi_R, const void* phi_L, cons
  * (at most 64).  Arrays may be host or device pointers; blocks the host.
  * TC_ERR_ARG if a norm or a pivot vanishes (outputs then undefined). */
 tc_status tc_biorthonormalize(tc_ctx* ctx, void* phi_R, void* phi_L, void* cuda_stream);
+
+/* One block-Davidson step for every k-point (Sec. 2.4), with a subspace of
+ * two blocks (p_max = 1, the paper's default block count).  The operator is
+ * h = T + the two- and three-body TC terms of tc_apply (right side) for the
+ * partners given by the first nocc bands of (phi_R, phi_L, occ), which stay
+ * fixed during the step; there is no pseudopotential.  Per k-point:
+ *   v_i = phi_R band i (i < nbands; orthonormal per k on entry);
+ *   w_i = P (h - eps_i) v_i, eps_i = <v_i|h|v_i>, Payne's preconditioner
+ *         P(x) = (27+18x+12x^2+8x^3)/(27+18x+12x^2+8x^3+16x^4),
+ *         x(G) = |k+G|^2/2 / <v_i|T|v_i> (P = 1 at |k+G| = 0 and 0 elsewhere
+ *         when <v_i|T|v_i> = 0);
+ *   each w_i orthogonalised against v and the w kept before it; kept if the
+ *   remaining norm is >= 1e-8 (so the subspace dimension d lies in
+ *   [nbands, 2 nbands]);
+ *   M_ab = <b_a|h|b_b> over b = (v, kept w); its right and left eigenvectors
+ *   y, z (z^H y = 1) for the nbands eigenvalues of lowest real part, in
+ *   ascending order of the real part;
+ *   phi_out_i = sum_a y_ai b_a, chi_out_i = sum_a z_ai b_a, then phi_out
+ *   orthonormalised by Gram-Schmidt and chi_out made biorthonormal to it
+ *   (as tc_biorthonormalize) -- the next step's trial vectors.
+ * Arguments: phi_R, phi_L, phi_out, chi_out are orbital arrays (layout above;
+ * host or device); the outputs must not alias the inputs or each other.
+ * occ: host [Nk][nbands] in [0, 1] (only the first nocc bands act as
+ * partners).  eig_out (optional): complex FP64 [Nk][nbands] Ritz values,
+ * host or device.  dim_out (optional): int [Nk] subspace dimensions, host or
+ * device.  The operator launches run in the context's precision; everything
+ * else in FP64.  The first call allocates the step's buffers and a second
+ * operator context with nocc + nbands bands (freed by tc_destroy).  At most 64
+ * bands.  Blocks the host until the results are complete.  TC_ERR_NUMERIC if
+ * the subspace eigen-solver does not converge or a Ritz vector set is
+ * singular (outputs then undefined). */
+tc_status tc_davidson_step(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, void* phi_out,
+                           void* chi_out, void* eig_out, int* dim_out, void* cuda_stream);
 
 /* Batched 3D FFT of `batch` contiguous n^3 complex volumes in place on the
  * device (precision TC_FP64: complex128, TC_FP32: complex64), sign -1

@@ -10,18 +10,21 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtc.so")
 
-TC_OK, TC_ERR_ARG, TC_ERR_STATE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED = range(7)
+(TC_OK, TC_ERR_ARG, TC_ERR_STATE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED,
+ TC_ERR_NUMERIC) = range(8)
 TC_FP64, TC_FP32 = 0, 1
 TERMS = ("2ah", "2bh1", "2bh2", "2ax", "2bx1", "2bx2", "3a1", "3a2", "3a3", "3a4",
          "3b1", "3b2", "3b3", "3b4", "3b5", "3b6")
 TC_NTERMS = 17          # 16 operator terms + kinetic
 EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d",
             "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
-            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info")
+            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
+            "tc_davidson_step")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",
-          TC_ERR_CUDA: "TC_ERR_CUDA", TC_ERR_TIMEOUT: "TC_ERR_TIMEOUT", TC_ERR_UNSUPPORTED: "TC_ERR_UNSUPPORTED"}
+          TC_ERR_CUDA: "TC_ERR_CUDA", TC_ERR_TIMEOUT: "TC_ERR_TIMEOUT", TC_ERR_UNSUPPORTED: "TC_ERR_UNSUPPORTED",
+          TC_ERR_NUMERIC: "TC_ERR_NUMERIC"}
 
 
 class tc_params(ctypes.Structure):
@@ -83,9 +86,11 @@ def load():
     lib.tc_apply_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(dp),
                                    ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     lib.tc_batch_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), dp]
+    lib.tc_davidson_step.argtypes = [vp, vp, vp, dp, vp, vp, vp, vp, vp]
     for name in ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
                  "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
-            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info"):
+            "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
+            "tc_davidson_step"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -89,6 +89,7 @@ void free_all(tc_ctx* c) {
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  if (c->occ_ev) cudaEventDestroy(c->occ_ev);
   if (c->h_occ) cudaFreeHost(c->h_occ);
   if (c->h_edot) cudaFreeHost(c->h_edot);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -155,7 +156,7 @@ __global__ void k_grad_combine(const double2* __restrict__ cphi, const double2* 
 // M_ij = <phi_i|chi_j> (Gauss-Jordan with partial pivoting on [M | I] in shared
 // memory), so that <chi_j|phi_l> = delta_jl.  *status = k + 1 if a norm or a
 // pivot vanishes at k-point k.
-constexpr int kBiorthoMaxBands = 64;
+using tc::kBiorthoMaxBands;
 
 __device__ double2 block_dot(const double2* a, const double2* b, int n, double* red) {
   // sum_g conj(a_g) b_g over the CTA; result valid in every thread
@@ -450,6 +451,7 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
   if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_status, sizeof(int)));
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_status, sizeof(int)));
   if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_edot, nj * sizeof(double2)));
+  if (e == cudaSuccess) ok(cudaEventCreateWithFlags(&c->occ_ev, cudaEventDisableTiming));
   if (e != cudaSuccess) {
     err = std::string("tc_init: ") + cudaGetErrorString(e);
     free_all(c);
@@ -471,16 +473,53 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
 void destroy_context(tc_ctx* c) {
   if (!c) return;
   if (c->batch) destroy_batch(c);
+  if (c->dav) destroy_davidson(c);
   free_all(c);
   delete c;
 }
 
 int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st) {
+  return apply_sides(c, phi, chi, outR, outL, 2, st);
+}
+
+int apply_sides(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, int nsides,
+                cudaStream_t st) {
   double tw[NT];
   term_weights(c, tw, 1.0, 1.0);
-  return c->prec == TC_FP64 ? dispatch_run<double>(c, phi, chi, outR, outL, tw, 2, st)
-                            : dispatch_run<float>(c, phi, chi, outR, outL, tw, 2, st);
+  return c->prec == TC_FP64 ? dispatch_run<double>(c, phi, chi, outR, outL, tw, nsides, st)
+                            : dispatch_run<float>(c, phi, chi, outR, outL, tw, nsides, st);
 }
+
+int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st) {
+  const size_t nj = (size_t)c->S.Nk * c->S.nb;
+  for (size_t i = 0; i < nj; ++i)
+    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return ::fail(c, TC_ERR_ARG, "occupations must lie in [0, 1]");
+  // the previous upload may not have run yet: h_occ is its source
+  if (c->occ_pending) {
+    const cudaError_t w = cudaEventSynchronize(c->occ_ev);
+    if (w != cudaSuccess) return cuda_fail(c, w, "occupation upload wait");
+  }
+  std::memcpy(c->h_occ, occ, nj * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(c->d_occ, c->h_occ, nj * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(c->occ_ev, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "occ upload");
+  c->occ_pending = true;
+  return TC_OK;
+}
+
+int launch_biortho(tc_ctx* c, double2* phi, double2* chi, int* status, cudaStream_t st) {
+  const Setup& S = c->S;
+  const size_t smem = (size_t)S.nb * 2 * S.nb * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_biortho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(c, e, "k_biortho attribute");
+  k_biortho<<<S.Nk, 256, smem, st>>>(phi, chi, c->d_npw, S.npw_max, S.nb, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "k_biortho");
+  return TC_OK;
+}
+
+bool device_ptr(const void* p) { return is_device_ptr(p); }
+
+tc_status fail(tc_ctx* c, tc_status s, const std::string& msg) { return ::fail(c, s, msg); }
 
 }  // namespace tc
 
@@ -519,12 +558,9 @@ static tc_status run_common(tc_ctx* c, const void* phi, const void* chi, const d
                             const double* tw, int nsides, cudaStream_t st, bool* host_out) {
   const tc::Setup& S = c->S;
   const size_t nj = (size_t)S.Nk * S.nb, orb = nj * S.npw_max * sizeof(double2);
-  for (size_t i = 0; i < nj; ++i) {
-    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return fail(c, TC_ERR_ARG, "occupations must lie in [0, 1]");
-    c->h_occ[i] = occ[i];
-  }
-  cudaError_t e = cudaMemcpyAsync(c->d_occ, c->h_occ, nj * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(c, e, "occ upload");
+  const int ro = tc::stage_occ(c, occ, st);
+  if (ro != TC_OK) return (tc_status)ro;
+  cudaError_t e = cudaSuccess;
   const double2* dphi = static_cast<const double2*>(phi);
   const double2* dchi = static_cast<const double2*>(chi);
   if (!is_device_ptr(phi)) {
@@ -775,11 +811,8 @@ tc_status tc_biorthonormalize(tc_ctx* c, void* phi, void* chi, void* stream) {
   if (hp && (e = cudaMemcpyAsync(dp, phi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
   if (hc && (e = cudaMemcpyAsync(dc, chi, orb, cudaMemcpyHostToDevice, st)) != cudaSuccess) return cuda_fail(c, e, "upload");
   if ((e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "status");
-  const size_t smem = (size_t)S.nb * 2 * S.nb * sizeof(double2);
-  if ((e = cudaFuncSetAttribute(k_biortho, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return cuda_fail(c, e, "k_biortho attribute");
-  k_biortho<<<S.Nk, 256, smem, st>>>(dp, dc, c->d_npw, S.npw_max, S.nb, c->d_status);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "k_biortho");
+  const int rb = tc::launch_biortho(c, dp, dc, c->d_status, st);
+  if (rb != TC_OK) return (tc_status)rb;
   int status = 0;
   if ((e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(c, e, "status");

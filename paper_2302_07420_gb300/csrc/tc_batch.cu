@@ -66,20 +66,6 @@ void destroy_batch(tc_ctx* c) {
 
 namespace {
 
-bool device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-tc_status fail(tc_ctx* c, tc_status s, const std::string& msg) {
-  c->err = msg;
-  return s;
-}
-
 // Cell indices in decreasing estimated cost.
 std::vector<int> by_cost(const BatchState* B) {
   std::vector<int> order(B->cells.size());

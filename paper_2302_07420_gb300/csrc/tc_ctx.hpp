@@ -8,6 +8,7 @@
 
 namespace tc {
 struct BatchState;
+struct DavState;
 // Offsets of the workspace pieces of one context inside its workspace block.
 struct WsLayout {
   size_t phi, chi, gphi, gchi, side, cs, scratch, total;
@@ -61,6 +62,11 @@ struct tc_ctx {
   // batch contexts (tc_init_batch): the cells and their shared workspace; nullptr otherwise
   tc::BatchState* batch = nullptr;
   bool batch_owner = false;        // a cell of a batch (destroyed with the batch)
+  // the last occupation upload from h_occ (h_occ is rewritten only after it has run)
+  cudaEvent_t occ_ev = nullptr;
+  bool occ_pending = false;
+  // block-Davidson buffers and the partner + new-vector operator context (first tc_davidson_step)
+  tc::DavState* dav = nullptr;
   // profiling (tc_profile / tc_stage_times)
   bool profile = false;
   cudaEvent_t ev[8] = {};
@@ -83,6 +89,17 @@ void ws_assign(tc_ctx* c, char* base, const WsLayout& L);
 // Both operator sides into outR / outL (device pointers) on st, all terms of term_mask.
 int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st);
 void destroy_batch(tc_ctx* c);
+void destroy_davidson(tc_ctx* c);
+// Validates occ (Nk*nb values in [0, 1]) and enqueues its upload into c->d_occ on st.
+int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st);
+// Operator on nsides sides (1: right only into outR; 2: both) for orbitals already on the device.
+int apply_sides(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, int nsides,
+                cudaStream_t st);
+// Biorthonormalises phi / chi (device, [Nk][nb][npw_max]) in place on st; *status <- k + 1 on failure at k.
+int launch_biortho(tc_ctx* c, double2* phi, double2* chi, int* status, cudaStream_t st);
+constexpr int kBiorthoMaxBands = 64;
+bool device_ptr(const void* p);
+tc_status fail(tc_ctx* c, tc_status s, const std::string& msg);
 void set_thread_error(const std::string& msg);
 
 // Runs the operator pipeline on the given stream.  tw: per-term weights;

@@ -149,6 +149,31 @@ class Context:
         _lib.check(self.lib, self.h, st)
         return phi_R, phi_L
 
+    def davidson_step(self, phi_R, phi_L, occ, stream=None):
+        """One block-Davidson step (tc_davidson_step): (phi, chi, eig (Nk, nbands) complex, dim (Nk,)).
+
+        Inputs and the returned orbitals are torch complex128 on the device, or numpy
+        arrays (then the outputs are numpy too); eig and dim are numpy arrays.
+        """
+        for x in (phi_R, phi_L):
+            self._check_orbitals(x)
+        if isinstance(phi_R, np.ndarray):
+            phi_R = np.ascontiguousarray(phi_R, dtype=np.complex128)
+            phi_L = np.ascontiguousarray(phi_L, dtype=np.complex128)
+            out_phi, out_chi = np.empty_like(phi_R), np.empty_like(phi_L)
+        else:
+            import torch
+            phi_R, phi_L = phi_R.contiguous(), phi_L.contiguous()
+            out_phi, out_chi = torch.empty_like(phi_R), torch.empty_like(phi_L)
+        occ_np, occ_p = self._occ(occ)
+        eig = np.empty((self.nk, self.nbands), dtype=np.complex128)
+        dim = np.empty(self.nk, dtype=np.int32)
+        st = self.lib.tc_davidson_step(self.h, _data_ptr(phi_R), _data_ptr(phi_L), occ_p, _data_ptr(out_phi),
+                                       _data_ptr(out_chi), ctypes.c_void_p(eig.ctypes.data),
+                                       ctypes.c_void_p(dim.ctypes.data), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return out_phi, out_chi, eig, dim
+
     def profile(self, enable=True):
         """Enable (and reset) or disable per-stage device timing."""
         _lib.check(self.lib, self.h, self.lib.tc_profile(self.h, 1 if enable else 0))
