@@ -293,6 +293,8 @@ def main():
                     help="skip the adjoint and 48^3 timings added to the line")
     ap.add_argument("--profile-run", action="store_true",
                     help="FP32 applies only (warm-up + steps), no JSON line: the ncu capture command")
+    ap.add_argument("--profile-davidson", action="store_true",
+                    help="FP32 Davidson steps only (warm-up + steps), no JSON line: the ncu capture command")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -333,6 +335,12 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    if args.profile_davidson:
+        for _ in range(args.warmup + args.steps):
+            ctx.davidson_step(d_phi, d_chi, occ)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     for _ in range(args.warmup):
         ctx.apply(d_phi, d_chi, occ, out_r, out_l)
     barrier()
