@@ -84,8 +84,10 @@ FOUR_PI = 4.0 * np.pi
 class TCOperator:
     """Right (left=False) or left (left=True) TC operator for fixed orbitals."""
 
-    def __init__(self, S, c_phi, c_chi, occ, left=False, backend=None, kset=None):
+    def __init__(self, S, c_phi, c_chi, occ, left=False, backend=None, kset=None, sym=None):
         self.S = S
+        # symmetry-reduced occupied-pair stage: (ops, kinfo, irred) of oracle.symmetry, or None
+        self.sym = sym
         self.bk = backend if backend is not None else FFTBackend(S)
         # Jastrow kernel data (values at S.A, S.C unless a displaced set is given, see gradient.py)
         self.ks = kset if kset is not None else KN.JastrowKernels(S.A, S.C)
@@ -179,7 +181,9 @@ class TCOperator:
         h6 = bk.zeros()
         h3a4 = [bk.zeros((no, 3)) for _ in range(Nk)]
         h3b = [bk.zeros((no, 3)) for _ in range(Nk)]
-        for k2 in range(Nk):
+        c6 = [bk.zeros() for _ in range(Nk)]              # h6 contribution of each q2's k-point
+        k2_list = range(Nk) if self.sym is None else self.sym[2]
+        for k2 in k2_list:
             for k1 in range(Nk):
                 # rhoA[q2, q1] = chi_q2^* phi_q1 (kernel at k1 - k2); rhoB[q1, q2] = chi_q1^* phi_q2
                 rhoA = bk.mul(bk.conj(self.bra[k2][:no])[:, None], self.ket[k1][:no][None])
@@ -193,7 +197,7 @@ class TCOperator:
                     PA = bk.iFT(KA["U"][s][None, None] * FA[:, :, None])   # P^s(q2,q1)  (no2, no1, 3)
                     PB = bk.iFT(KB["U"][s][None, None] * FB[:, :, None])   # P^s(q1,q2)  (no1, no2, 3)
                     prod = np.sum(bk.mul(PA, np.swapaxes(PB, 0, 1)), axis=2)  # (no2, no1)
-                    h6 = h6 + np.sum(w[:, :, None, None, None] * prod, axis=(0, 1))
+                    c6[k2] = c6[k2] + np.sum(w[:, :, None, None, None] * prod, axis=(0, 1))
                     if s == 0:
                         f1 = self.f[k1] / Nk
                         # h3(q2) += f1 P^pp(q1,q2) phi_q1            (Alg. 6 line 8)
@@ -203,7 +207,21 @@ class TCOperator:
                         t = bk.mul(PA, bk.conj(self.bra[k1][:no])[None, :, None])
                         h3b[k2] = h3b[k2] + np.sum(f1[None, :, None, None, None, None] * t, axis=1)
         if S.div_correction:
-            h6 = h6 + self._corr_3a2()
+            for k2 in k2_list:
+                c6[k2] = c6[k2] + self._corr_3a2(k2)
+        if self.sym is not None:
+            # Sec. 2.6.4: fields of q2 from those of its irreducible q2;0
+            from . import symmetry as SY
+            ops, kinfo, _ = self.sym
+            for k2 in range(Nk):
+                k0, op, tr, K = kinfo[k2]
+                if k2 == k0:
+                    continue
+                h3a4[k2] = SY.rotate_field(S, h3a4[k0], ops[op], tr, K, vector=True)
+                h3b[k2] = SY.rotate_field(S, h3b[k0], ops[op], tr, -K, vector=True)
+                c6[k2] = SY.rotate_field(S, c6[k0], ops[op], tr, 0 * K, vector=False)
+        for k2 in range(Nk):
+            h6 = h6 + c6[k2]
         self.h6 = h6
         self.h3a4 = h3a4
         self.h3b = h3b
@@ -215,24 +233,23 @@ class TCOperator:
         self.h5 = h5
         self.t3b2 = bk.iFT(np.sum(-self.Uh * bk.FT(h5), axis=0))
 
-    def _corr_3a2(self):
-        """Eqs. divcor_3a2_first/second (general-overlap form), summed into h6."""
+    def _corr_3a2(self, k):
+        """Eqs. divcor_3a2_first/second (general-overlap form) of the q2 at k-point k, added to h6."""
         S, bk = self.S, self.bk
         Nk, no, Om = S.Nk, S.nocc, S.Omega
         out = bk.zeros()
-        for k in range(Nk):
-            rho = bk.mul(bk.conj(self.bra[k][:no])[:, None], self.ket[k][:no][None])  # [a, b] = chi_a^* phi_b
-            F = bk.FT(rho)
-            O = bk.spec_at_zero(F)                                                      # <chi_a|phi_b>
-            f = self.f[k]
-            for q2 in range(no):
-                F0 = np.sum(f * O[q2, :] * O[:, q2])
-                Fa = np.sum((f * O[:, q2])[:, None, None, None] * F[q2, :], axis=0)  # FT[chi_q2^* phi_q1](G) <chi_q1|phi_q2>
-                Fb = np.sum((f * O[q2, :])[:, None, None, None] * F[:, q2], axis=0)  # <chi_q2|phi_q1> FT[chi_q1^* phi_q2](G)
-                for s in range(2):
-                    c = self.ks.corr(s, S.Gamma0, S.ushort_factor, Nk)
-                    field = bk.const(c * F0) + (FOUR_PI * self.ks.amp(s) / Nk) * bk.iFT(self.us[s] * (Fa + Fb))
-                    out = out + (f[q2] / Nk) * field / (Om * Om)
+        rho = bk.mul(bk.conj(self.bra[k][:no])[:, None], self.ket[k][:no][None])  # [a, b] = chi_a^* phi_b
+        F = bk.FT(rho)
+        O = bk.spec_at_zero(F)                                                      # <chi_a|phi_b>
+        f = self.f[k]
+        for q2 in range(no):
+            F0 = np.sum(f * O[q2, :] * O[:, q2])
+            Fa = np.sum((f * O[:, q2])[:, None, None, None] * F[q2, :], axis=0)  # FT[chi_q2^* phi_q1](G) <chi_q1|phi_q2>
+            Fb = np.sum((f * O[q2, :])[:, None, None, None] * F[:, q2], axis=0)  # <chi_q2|phi_q1> FT[chi_q1^* phi_q2](G)
+            for s in range(2):
+                c = self.ks.corr(s, S.Gamma0, S.ushort_factor, Nk)
+                field = bk.const(c * F0) + (FOUR_PI * self.ks.amp(s) / Nk) * bk.iFT(self.us[s] * (Fa + Fb))
+                out = out + (f[q2] / Nk) * field / (Om * Om)
         return out
 
     # ------------------------------------------------------------------ apply
@@ -346,8 +363,8 @@ class TCOperator:
         return out
 
 
-def apply_operator(S, c_phi, c_chi, occ, left=False, kpoints=None, terms=TERMS, backend=None, kset=None):
-    op = TCOperator(S, c_phi, c_chi, occ, left=left, backend=backend(S) if backend else None, kset=kset)
+def apply_operator(S, c_phi, c_chi, occ, left=False, kpoints=None, terms=TERMS, backend=None, kset=None, sym=None):
+    op = TCOperator(S, c_phi, c_chi, occ, left=left, backend=backend(S) if backend else None, kset=kset, sym=sym)
     return op.apply(kpoints=kpoints, terms=terms)
 
 

@@ -173,3 +173,88 @@ def occupations(Nk, nbands, nocc, fill=1.0):
     occ = np.zeros((Nk, nbands))
     occ[:, :nocc] = fill
     return occ
+
+
+# ---------------------------------------------------------------------------
+# Crystal-symmetric inputs.  Orbitals that obey the point group of a crystal
+# come from diagonalising a model one-body operator that has that symmetry:
+#   h(k)_{GG'} = |k+G|^2/2 delta_GG' + V(G - G') - lam W(G - G') (G - G').(k + G'),
+#   V(Q) = v0 (|Q|^2 - qc2) exp(-|Q|^2/sv^2) s(Q),  W(Q) = w0 exp(-|Q|^2/sw^2) s(Q),
+#   s(Q) = (1/n_at) sum_atoms exp(-i Q.tau_a),
+# i.e. T + V(r) + lam grad W(r) . grad with V, W sums of spherical atomic
+# functions: real in real space (time-reversal symmetric) and non-Hermitian
+# for lam != 0 (a TC-like first-order term).  Right / left eigenvectors of the
+# nbands eigenvalues of lowest real part, per k-point, give phi (Gram-Schmidt)
+# and chi (biorthonormal to phi); a gap after band nbands at every k-point
+# makes the occupied spaces symmetric.
+
+SI_ATOMS = ((0.0, 0.0, 0.0), (0.25, 0.25, 0.25))   # diamond structure, fractional coordinates
+
+
+def point_group(lattice, atoms_frac=SI_ATOMS):
+    """Integer matrices S (x -> S x on fractional real-space coordinates) that keep the
+    lattice metric and map the atom set onto itself (modulo lattice vectors); identity first."""
+    import itertools
+    L = np.asarray(lattice, dtype=np.float64)
+    M = L @ L.T
+    cand = np.array(list(itertools.product((-1, 0, 1), repeat=9)), dtype=np.int64).reshape(-1, 3, 3)
+    lhs = np.einsum("nji,jk,nkl->nil", cand, M, cand)
+    keep = np.all(np.abs(lhs - M[None]) <= 1e-9 * np.abs(M).max(), axis=(1, 2))
+    cand = cand[keep]
+    X = np.asarray(atoms_frac, dtype=np.float64)
+    ops = []
+    for S in cand:
+        Y = X @ S.T
+        ok = True
+        for y in Y:
+            d = X - y[None]
+            if not np.any(np.all(np.abs(d - np.round(d)) < 1e-9, axis=1)):
+                ok = False
+                break
+        if ok:
+            ops.append(S)
+    ops.sort(key=lambda S: (0 if np.array_equal(S, np.eye(3, dtype=np.int64)) else 1, tuple(S.ravel())))
+    return np.array(ops, dtype=np.int64)
+
+
+MODEL = dict(v0=0.16, qc2=2.0, sv=1.5, w0=0.05, sw=1.5, lam=1.0)
+
+
+def model_orbitals(lattice, kcart, miller_list, npw_max, nbands, atoms_frac=SI_ATOMS, model=None):
+    """(c_phi, c_chi, eig (Nk, nbands+1) complex, gap): symmetric model orbitals on the given spheres.
+
+    kcart: (Nk, 3) Cartesian k; miller_list[k]: (npw_k, 3) Miller indices of the sphere.
+    gap = min over k of Re eig[nbands] - Re eig[nbands-1] (must be > 0 for symmetric occupied spaces).
+    """
+    prm = dict(MODEL, **(model or {}))
+    L = np.asarray(lattice, dtype=np.float64)
+    B = 2.0 * np.pi * np.linalg.inv(L).T
+    tau = np.asarray(atoms_frac, dtype=np.float64) @ L
+    Nk = len(miller_list)
+    c_phi = np.zeros((Nk, nbands, npw_max), dtype=np.complex128)
+    c_chi = np.zeros_like(c_phi)
+    eig = np.zeros((Nk, nbands + 1), dtype=np.complex128)
+    gap = np.inf
+    for k in range(Nk):
+        G = np.asarray(miller_list[k], dtype=np.float64) @ B
+        kG = kcart[k][None] + G
+        Q = G[:, None, :] - G[None, :, :]
+        q2 = np.einsum("ijd,ijd->ij", Q, Q)
+        sf = np.mean(np.exp(-1j * np.einsum("ijd,ad->ija", Q, tau)), axis=2)
+        V = prm["v0"] * (q2 - prm["qc2"]) * np.exp(-q2 / prm["sv"] ** 2) * sf
+        W = prm["w0"] * np.exp(-q2 / prm["sw"] ** 2) * sf
+        H = V - prm["lam"] * W * np.einsum("ijd,jd->ij", Q, kG)
+        H[np.diag_indices_from(H)] += 0.5 * np.einsum("id,id->i", kG, kG)
+        lam_, Y = np.linalg.eig(H)
+        order = np.argsort(lam_.real, kind="stable")
+        lam_, Y = lam_[order], Y[:, order]
+        Z = np.linalg.inv(Y).conj().T
+        eig[k] = lam_[: nbands + 1]
+        gap = min(gap, lam_[nbands].real - lam_[nbands - 1].real)
+        P = _gram_schmidt(Y[:, :nbands])
+        Xp = Z[:, :nbands]
+        X = Xp @ np.linalg.inv(P.conj().T @ Xp)
+        n = G.shape[0]
+        c_phi[k, :, :n] = P.T
+        c_chi[k, :, :n] = X.T
+    return c_phi, c_chi, eig, gap
