@@ -52,8 +52,8 @@ def pairs_per_apply(nk, nb, no):
     return 2 * ((nk * nb) * (nk * no) + (nk * no) ** 2)
 
 
-def kpg_list(lattice, kmesh, miller, npw):
-    """k+G of each sphere from the layout (Gamma-centred mesh, fractions in (-1/2, 1/2])."""
+def kmesh_cart(lattice, kmesh):
+    """Cartesian k of the Gamma-centred mesh (fractions in (-1/2, 1/2]) in the library's k order."""
     B = 2.0 * np.pi * np.linalg.inv(np.asarray(lattice)).T
     fr = []
     for a in range(kmesh[0]):
@@ -61,7 +61,69 @@ def kpg_list(lattice, kmesh, miller, npw):
             for c in range(kmesh[2]):
                 f = np.array([a / kmesh[0], b / kmesh[1], c / kmesh[2]])
                 fr.append(np.where(f > 0.5, f - 1.0, f))
-    return [np.asarray(fr[k]) @ B + miller[k, : npw[k]] @ B for k in range(len(fr))]
+    return np.array(fr) @ B
+
+
+def kpg_list(lattice, kmesh, miller, npw):
+    """k+G of each sphere from the layout."""
+    B = 2.0 * np.pi * np.linalg.inv(np.asarray(lattice)).T
+    kc = kmesh_cart(lattice, kmesh)
+    return [kc[k] + miller[k, : npw[k]] @ B for k in range(len(kc))]
+
+
+def measure_symmetric(p, dev, steps=5):
+    """Same cell with symmetric model orbitals (diamond point group T_d + time reversal): FP32 apply with
+    the symmetry-reduced occupied-pair stage and without it, device-timed, and their difference."""
+    import torch
+    from paper_2302_07420_gb300 import synth
+    from paper_2302_07420_gb300.operator import Context
+    ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                  precision="fp32")
+    npw, miller = ctx.layout()
+    kc = kmesh_cart(p["lattice"], p["kmesh"])
+    cp, cc, eig, gap = synth.model_orbitals(p["lattice"], kc, [miller[k, : npw[k]] for k in range(ctx.nk)],
+                                            ctx.npw_max, p["nbands"])
+    ops = synth.point_group(p["lattice"])
+    occ = synth.occupations(ctx.nk, p["nbands"], p["nocc"])
+    a, b = torch.from_numpy(cp).to(dev), torch.from_numpy(cc).to(dev)
+    ctx.set_symmetry(ops)
+    nirr, _ = ctx.symmetry_info()
+    ctx.symmetrize_orbitals(a, b)
+    out = {}
+    res = {}
+    for mode in ("reduced", "full"):
+        if mode == "full":
+            ctx.set_symmetry([])
+        r, l = ctx.apply(a, b, occ)
+        for _ in range(2):
+            ctx.apply(a, b, occ, r, l)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            ctx.apply(a, b, occ, r, l)
+        e1.record()
+        torch.cuda.synchronize()
+        res[mode] = (e0.elapsed_time(e1) / steps, r.clone(), l.clone())
+        ctx.davidson_step(a, b, occ)
+        t0 = time.perf_counter()
+        ctx.davidson_step(a, b, occ)
+        res[mode + "_dav"] = 1e3 * (time.perf_counter() - t0)
+    ctx.close()
+    nk, nb, no = len(kc), p["nbands"], p["nocc"]
+    npairs = pairs_per_apply(nk, nb, no)
+    sc = max(float(res["full"][1].abs().max()), float(res["full"][2].abs().max()))
+    diff = max(float((res["reduced"][1] - res["full"][1]).abs().max()),
+               float((res["reduced"][2] - res["full"][2]).abs().max())) / sc
+    out = {"what": "same cell, symmetric model orbitals (T_d, 24 operations, + time reversal); FP32 apply (R+L) "
+                   "with the occupied-pair stage and the outputs over irreducible k-points only vs over all",
+           "irreducible_k": nirr, "ms_reduced": res["reduced"][0], "ms_full": res["full"][0],
+           "pairs_per_s_reduced": npairs / (res["reduced"][0] / 1e3),
+           "pairs_per_s_full": npairs / (res["full"][0] / 1e3),
+           "occupied_pairs_computed_reduced": 2 * (nirr * no) * (nk * no),
+           "max_rel_diff_reduced_vs_full": diff, "model_gap_ha": float(gap),
+           "davidson_step_ms_reduced": res["reduced_dav"], "davidson_step_ms_full": res["full_dav"]}
+    return out
 
 
 class ClockSampler:
@@ -171,6 +233,7 @@ def measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev):
                             "ms": 1e3 * td, "subspace_dim": [int(dim.min()), int(dim.max())],
                             "pair_chains": one_side + (nk * (no + nb)) * (nk * no),
                             "lowest_ritz_value_k0": float(eig[0, 0].real)}
+    out["symmetric"] = measure_symmetric(p, dev)
     h = synth.WORKLOADS["heg_114"]()
     hc = Context(h["lattice"], h["kmesh"], h["ecut"], h["fft"], h["nbands"], h["nocc"], h["A"], h["C"],
                  precision="fp32")
@@ -293,6 +356,8 @@ def main():
                     help="skip the adjoint and 48^3 timings added to the line")
     ap.add_argument("--profile-run", action="store_true",
                     help="FP32 applies only (warm-up + steps), no JSON line: the ncu capture command")
+    ap.add_argument("--symmetric", action="store_true",
+                    help="with --profile-run: symmetric model orbitals and the T_d + time-reversal reduction")
     ap.add_argument("--profile-davidson", action="store_true",
                     help="FP32 Davidson steps only (warm-up + steps), no JSON line: the ncu capture command")
     args = ap.parse_args()
@@ -344,6 +409,17 @@ def main():
     for _ in range(args.warmup):
         ctx.apply(d_phi, d_chi, occ, out_r, out_l)
     barrier()
+    if args.profile_run and args.symmetric:
+        kc = kmesh_cart(p["lattice"], p["kmesh"])
+        cp, cc, _, _ = synth.model_orbitals(p["lattice"], kc, [miller[k, : npw[k]] for k in range(ctx.nk)],
+                                            ctx.npw_max, p["nbands"])
+        d_phi.copy_(torch.from_numpy(cp))
+        d_chi.copy_(torch.from_numpy(cc))
+        ctx.set_symmetry(synth.point_group(p["lattice"]))
+        ctx.symmetrize_orbitals(d_phi, d_chi)
+        for _ in range(args.warmup):
+            ctx.apply(d_phi, d_chi, occ, out_r, out_l)
+        torch.cuda.synchronize()
     if args.profile_run:
         for _ in range(args.steps):
             ctx.apply(d_phi, d_chi, occ, out_r, out_l)

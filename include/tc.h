@@ -183,6 +183,36 @@ tc_status tc_biorthonormalize(tc_ctx* ctx, void* phi_R, void* phi_L, void* cuda_
 tc_status tc_davidson_step(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, void* phi_out,
                            void* chi_out, void* eig_out, int* dim_out, void* cuda_stream);
 
+/* Crystal symmetry (Sec. 2.3 end, Sec. 2.6.4).  rot: nops integer 3x3
+ * matrices S, row-major, acting on fractional real-space coordinates
+ * (x -> S x; symmorphic operations, no translation); they must include the
+ * identity, keep the lattice metric and map the k mesh onto itself.
+ * time_reversal != 0 adds k -> -k.  The mesh points are taken in order; a
+ * point that no earlier irreducible point reaches is irreducible, and its
+ * images under the operations (then, with time reversal, the operations
+ * times -1), in the given order, claim the points they reach first:
+ * k = tr S^T k0 - K with tr = +-1 and K an integer vector (reciprocal
+ * fractional coordinates).  From then on tc_apply / tc_energy /
+ * tc_energy_grad / tc_davidson_step compute the occupied-pair stage
+ * (Algs. 4, 6, 8, 11) for irreducible q2 only and obtain the other q2 by
+ * rotation, which is exact when the orbitals obey the symmetry (as
+ * tc_symmetrize_orbitals makes them); other inputs give undefined results.
+ * Needs the pair densities to fit the FFT box without wrapping (the Miller
+ * span of all spheres, per axis, at most n/2 - 1), else TC_ERR_UNSUPPORTED.
+ * nops = 0 switches the reduction off.  Synchronises the device and may
+ * re-allocate the workspace (a different partner-chunk count).  Not for
+ * batch contexts (TC_ERR_STATE). */
+tc_status tc_set_symmetry(tc_ctx* ctx, int nops, const int* rot, int time_reversal);
+/* Number of irreducible k-points and, if kmap6 is not NULL, per k-point
+ * {k0, operation, tr, K1, K2, K3} (host int [Nk][6]); without symmetry every
+ * point is its own (identity, tr = 1, K = 0). */
+tc_status tc_symmetry_info(const tc_ctx* ctx, int* nirr, int* kmap6);
+/* Overwrites the orbitals of every non-irreducible k-point (all bands, phi_R
+ * and phi_L alike) by those of its irreducible point (Sec. 2.3):
+ * c_k(tr S^T m0 + K) = c_k0(m0), conjugated when tr = -1.  Host or device
+ * pointers; with host pointers the call returns after the copies. */
+tc_status tc_symmetrize_orbitals(tc_ctx* ctx, void* phi_R, void* phi_L, void* cuda_stream);
+
 /* Batched 3D FFT of `batch` contiguous n^3 complex volumes in place on the
  * device (precision TC_FP64: complex128, TC_FP32: complex64), sign -1
  * (sum f e^{-2 pi i m.r/n}) or +1; unnormalised.  Exposes the library's

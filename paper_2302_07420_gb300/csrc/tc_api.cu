@@ -371,6 +371,33 @@ void choose_splits(tc_ctx* c) {
   c->sc_max = std::max(c->split_chain[0], c->split_chain[1]);
 }
 
+int pick_split_for(int items, int partners, int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return pick_split(items, partners, sms);
+}
+
+// Replaces the owned workspace block by one laid out for the current split counts.
+int rebuild_workspace(tc_ctx* c) {
+  if (!c->ws_owned) return TC_ERR_STATE;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && c->d_ws) e = cudaFree(c->d_ws);
+  c->d_ws = nullptr;
+  const WsLayout L = ws_layout(c);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_ws, L.total);
+  if (e == cudaSuccess) e = cudaMemset(c->d_ws, 0, L.total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->err = std::string("workspace: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TC_ERR_OOM : TC_ERR_CUDA;
+  }
+  ws_assign(c, static_cast<char*>(c->d_ws), L);
+  return TC_OK;
+}
+
 void ws_assign(tc_ctx* c, char* base, const WsLayout& L) {
   c->d_phi = base + L.phi;
   c->d_chi = base + L.chi;
@@ -474,6 +501,7 @@ void destroy_context(tc_ctx* c) {
   if (!c) return;
   if (c->batch) destroy_batch(c);
   if (c->dav) destroy_davidson(c);
+  free_symmetry(c);
   free_all(c);
   delete c;
 }

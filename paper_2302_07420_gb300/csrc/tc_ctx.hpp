@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "tc_setup.hpp"
 
@@ -62,6 +63,14 @@ struct tc_ctx {
   // batch contexts (tc_init_batch): the cells and their shared workspace; nullptr otherwise
   tc::BatchState* batch = nullptr;
   bool batch_owner = false;        // a cell of a batch (destroyed with the batch)
+  // crystal symmetry (tc_set_symmetry): maps and tables on the device, 0 / nullptr when off
+  int sym = 0, nirr = 0;
+  std::vector<int> sym_ops;        // host copy of the operations [nops][9] and the time-reversal flag
+  int sym_tr = 0, sym_version = 0; // version: incremented by every tc_set_symmetry
+  int *d_irr = nullptr, *d_symk = nullptr, *d_symrot = nullptr, *d_star_off = nullptr, *d_star_k = nullptr;
+  int* d_sym_src = nullptr;        // [Nk][npw_max] sphere index at k0 of each coefficient at k (-1 pad)
+  double* d_symcart64 = nullptr;   // [nops][9]
+  float* d_symcart32 = nullptr;
   // the last occupation upload from h_occ (h_occ is rewritten only after it has run)
   cudaEvent_t occ_ev = nullptr;
   bool occ_pending = false;
@@ -90,6 +99,10 @@ void ws_assign(tc_ctx* c, char* base, const WsLayout& L);
 int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st);
 void destroy_batch(tc_ctx* c);
 void destroy_davidson(tc_ctx* c);
+void free_symmetry(tc_ctx* c);
+// Overwrites the coefficient arrays a, b ([Nk][nb][npw_max], device; b may be null) at every
+// non-irreducible k-point by the symmetry image of its irreducible point.
+int launch_sym_unfold(tc_ctx* c, double2* a, double2* b, cudaStream_t st);
 // Validates occ (Nk*nb values in [0, 1]) and enqueues its upload into c->d_occ on st.
 int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st);
 // Operator on nsides sides (1: right only into outR; 2: both) for orbitals already on the device.

@@ -47,6 +47,7 @@ struct DavState {
   int* h_dim = nullptr;
   int* h_status = nullptr;
   std::vector<double> occ_aux;        // host [Nk][nocc + m]
+  int aux_sym_version = 0;            // the context's symmetry version last given to aux
   size_t eig_words = 0;               // double2 words of the solver's arrays per k
   bool eig_in_smem = true;
 };
@@ -572,6 +573,14 @@ __global__ void __launch_bounds__(kEigThreads) k_dav_subspace(
   if (threadIdx.x == 0) dim_out[k] = d;
 }
 
+// With crystal symmetry: every k-point takes the kept-vector count of its irreducible point.
+__global__ void k_dav_sym_cnt(int* cnt, const int* __restrict__ symk, int Nk) {
+  for (int k = threadIdx.x; k < Nk; k += blockDim.x) {
+    const int k0 = symk[6 * k];
+    if (k0 != k) cnt[k] = cnt[k0];
+  }
+}
+
 // phi_s = sum_a Y_as b_a, chi_s = sum_a Z_as b_a; one thread per plane wave.
 __global__ void k_dav_rotate(const double2* __restrict__ v, const double2* __restrict__ w, const double2* __restrict__ Y,
                              const double2* __restrict__ Z, const int* __restrict__ dim_k, const int* __restrict__ npw_k,
@@ -695,6 +704,21 @@ tc_status tc_davidson_step(tc_ctx* c, const void* phi, const void* chi, const do
   k_dav_expand<<<S.Nk, kDavThreads, 0, st>>>(dphi, dchi, D->hv, c->d_kpg, c->d_npw, S.npw_max, m, no, D->w,
                                               D->aux_phi, D->aux_chi, D->cnt);
   if ((e = cudaGetLastError()) != cudaSuccess) return dav_cuda(c, e, "k_dav_expand");
+  if (D->aux_sym_version != c->sym_version) {
+    // the second operator context takes the same symmetry (it reduces h w as the first launch reduces h v)
+    const int nops = (int)(c->sym_ops.size() / 9);
+    const tc_status rs = tc_set_symmetry(D->aux, c->sym ? nops : 0, c->sym ? c->sym_ops.data() : nullptr, c->sym_tr);
+    if (rs != TC_OK) return dav_fail(c, rs, "Davidson operator context: " + D->aux->err);
+    D->aux_sym_version = c->sym_version;
+  }
+  if (c->sym) {
+    // new vectors of the other k-points by symmetry, so that both launches see one symmetric set
+    k_dav_sym_cnt<<<1, 128, 0, st>>>(D->cnt, c->d_symk, S.Nk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return dav_cuda(c, e, "k_dav_sym_cnt");
+    int ru = tc::launch_sym_unfold(c, D->w, nullptr, st);
+    if (ru == TC_OK) ru = tc::launch_sym_unfold(D->aux, D->aux_phi, D->aux_chi, st);
+    if (ru != TC_OK) return (tc_status)ru;
+  }
   // 3. h w with the same partners
   for (size_t k = 0; k < Nk; ++k)
     for (int b = 0; b < na; ++b) D->occ_aux[k * na + b] = b < no ? occ[k * m + b] : 0.0;
@@ -718,6 +742,7 @@ tc_status tc_davidson_step(tc_ctx* c, const void* phi, const void* chi, const do
   if ((e = cudaMemsetAsync(D->status, 0, sizeof(int), st)) != cudaSuccess) return dav_cuda(c, e, "status");
   rr = tc::launch_biortho(c, ophi, ochi, D->status, st);
   if (rr != TC_OK) return (tc_status)rr;
+  if (c->sym && (rr = tc::launch_sym_unfold(c, ophi, ochi, st)) != TC_OK) return (tc_status)rr;
   // outputs
   if (hp && (e = cudaMemcpyAsync(phi_out, ophi, orb, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return dav_cuda(c, e, "phi download");

@@ -60,6 +60,14 @@ template <typename T> struct Params {
   const T* hartUs;       // [2][N] (no 1/Omega)
   const double* occ;     // [Nk][nb]
   cplx<T>* scratch;      // per-CTA volumes
+  // crystal symmetry of the occupied-pair stage (tc_set_symmetry); sym = 0: every q2 computed
+  int sym, nirr;
+  const int* irr;        // [nirr] irreducible k-points, ascending
+  const int* symk;       // [Nk][6]: k0, operation, tr (+1 / -1), K (3 integers)
+  const int* symrot;     // [nops][9] fractional operation S (x -> S x), row-major
+  const T* symcart;      // [nops][9] Cartesian S^dagger = S_c^T, row-major
+  const int* star_off;   // [nirr + 1] offsets into star_k
+  const int* star_k;     // [Nk] k-points grouped by their irreducible point
   SideArgs<T> side[2];
 };
 

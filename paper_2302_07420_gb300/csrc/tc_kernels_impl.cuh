@@ -268,7 +268,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   __shared__ double sF0[2];
   const SideArgs<T>& S = P.side[blockIdx.y];
   const int M = P.Nk * P.no;                                   // occupied states
-  const int i2 = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
+  // with crystal symmetry only the q2 of irreducible k-points have CTAs (the rest are unfolded)
+  const int item = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
+  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : item;
   const int k2 = i2 / P.no, mu2 = i2 % P.no;
   const int q2 = k2 * P.nb + mu2;
   const int i1_begin = (int)((long long)chunk * M / P.so), i1_end = (int)((long long)(chunk + 1) * M / P.so);
@@ -330,9 +332,10 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
       // The antiparallel channel only feeds h6, and its contribution P^ap(q2,q1) . P^ap(q1,q2) is
       // symmetric in (q1, q2): each unordered pair is taken once, by the CTA for which q1 lies
       // in the next half of the cyclic order after q2, with weight 2 (1 on the diagonal).
+      // (With symmetry the part of each irreducible q2 must hold all its pairs: no halving.)
       const int cyc = (i1 - i2 + M) % M;
-      const bool ap_here = cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
-      const T ap_w = cyc == 0 ? T(1) : T(2);
+      const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
+      const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
       for (int sp = 0; sp < 2; ++sp) {
         if (sp == 1 && !ap_here) continue;
         const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
@@ -401,19 +404,46 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   }
 }
 
-// h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8 lines 9-10)
+// Grid index of the image S x of grid point (i1, i2, i3) under a fractional operation S.
+template <int N> __device__ __forceinline__ int sym_image(const int* R, int i1, int i2, int i3) {
+  int y[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int v = (R[3 * a] * i1 + R[3 * a + 1] * i2 + R[3 * a + 2] * i3) % N;
+    y[a] = v < 0 ? v + N : v;
+  }
+  return (y[0] * N + y[1]) * N + y[2];
+}
+
+// h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8 lines 9-10).
+// With symmetry the part of an irreducible q2;0 stands for every q2 of its star:
+// part(q2)(x) = part(q2;0)(S x), conjugated under time reversal (Sec. 2.6.4).
 template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
   using G = Geo<N>;
   constexpr int NS = 6;
   const int side = blockIdx.y;
   const SideArgs<T>& S = P.side[side];
   const size_t NN = G::nn;
-  const int M = P.Nk * P.no, ncta = M * P.so;   // k_occ_pairs CTAs per side
+  const int M = P.Nk * P.no, ncta = (P.sym ? P.nirr * P.no : M) * P.so;   // k_occ_pairs CTAs per side
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < (int)NN; r += gridDim.x * blockDim.x) {
     cplx<T> h6 = {0, 0}, h5[3] = {{0, 0}, {0, 0}, {0, 0}};
-    for (int c = 0; c < ncta; ++c) {
-      const size_t cta = (size_t)side * ncta + c;
-      h6 = h6 + P.scratch[(cta * NS + 4) * (size_t)Geo<N>::vol + r];
+    if (!P.sym) {
+      for (int c = 0; c < ncta; ++c) {
+        const size_t cta = (size_t)side * ncta + c;
+        h6 = h6 + P.scratch[(cta * NS + 4) * (size_t)Geo<N>::vol + r];
+      }
+    } else {
+      const int i1 = r / (N * N), i2 = (r / N) % N, i3 = r % N;
+      for (int c = 0; c < ncta; ++c) {
+        const int b = c / (P.no * P.so);
+        const cplx<T>* part = P.scratch + (((size_t)side * ncta + c) * NS + 4) * (size_t)Geo<N>::vol;
+        for (int t = P.star_off[b]; t < P.star_off[b + 1]; ++t) {
+          const int* e = P.symk + 6 * P.star_k[t];
+          cplx<T> v = part[sym_image<N>(P.symrot + 9 * e[1], i1, i2, i3)];
+          if (e[2] < 0) v.y = -v.y;
+          h6 = h6 + v;
+        }
+      }
     }
     for (int c = 0; c < M; ++c) {
       const int k = c / P.no, mu = c % P.no;
@@ -426,6 +456,46 @@ template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
     S.h6[r] = h6;
 #pragma unroll
     for (int d = 0; d < 3; ++d) S.h5[d * NN + r] = h5[d];
+  }
+}
+
+// Occupied-pair fields of every q2 at a non-irreducible k-point from those of its q2;0
+// (Sec. 2.6.4, Eqs. symope_3a2_1/2), on the real-space grid: with k2 = tr S^T k0 - K,
+//   h3a4(q2)(x) = e^{+2 pi i K.x} S_c^T [conj] h3a4(q2;0)(S x)   (crystal momentum +k2)
+//   h3b(q2)(x)  = e^{-2 pi i K.x} S_c^T [conj] h3b(q2;0)(S x)    (crystal momentum -k2)
+// (conjugation under time reversal), written into part 0 after the parts are summed.
+template <typename T, int N> __global__ void k_unfold(Params<T> P) {
+  const SideArgs<T>& S = P.side[blockIdx.y];
+  const size_t NN = (size_t)N * N * N;
+  const size_t total = (size_t)P.Nk * P.no * NN;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int q2 = (int)(e / NN), r = (int)(e % NN);
+    const int k2 = q2 / P.no, mu = q2 % P.no;
+    const int* m = P.symk + 6 * k2;
+    if (m[0] == k2) continue;
+    const int i1 = r / (N * N), i2 = (r / N) % N, i3 = r % N;
+    const int y = sym_image<N>(P.symrot + 9 * m[1], i1, i2, i3);
+    int kx = (m[3] * i1 + m[4] * i2 + m[5] * i3) % N;
+    if (kx < 0) kx += N;
+    double sn = 0.0, cs = 1.0;
+    if (kx != 0) sincospi(2.0 * kx / N, &sn, &cs);
+    const T* C = P.symcart + 9 * m[1];
+    const size_t src = ((size_t)m[0] * P.no + mu) * 3, dst = (size_t)q2 * 3;
+    for (int kind = 0; kind < 2; ++kind) {
+      cplx<T>* h = kind == 0 ? S.h3a4 : S.h3b;
+      cplx<T> v[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        v[d] = h[(src + d) * NN + y];
+        if (m[2] < 0) v[d].y = -v[d].y;
+      }
+      const cplx<T> ph = {(T)cs, (T)(kind == 0 ? sn : -sn)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const cplx<T> o = C[3 * d] * v[0] + C[3 * d + 1] * v[1] + C[3 * d + 2] * v[2];
+        h[(dst + d) * NN + r] = ph * o;
+      }
+    }
   }
 }
 
@@ -511,7 +581,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   __shared__ T red[32];
   const SideArgs<T>& S = P.side[blockIdx.y];
-  const int j = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc, kj = j / P.nb;
+  // with crystal symmetry only orbitals of irreducible k-points are computed (the rest are unfolded)
+  const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
+  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
   const int M = P.Nk * P.no, nj = P.Nk * P.nb;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
@@ -702,7 +774,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smraw);
   const SideArgs<T>& S = P.side[blockIdx.y];
-  const int j = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc, kj = j / P.nb;
+  // with crystal symmetry only orbitals of irreducible k-points are computed (the rest are unfolded)
+  const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
+  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
   const int M = P.Nk * P.no, nj = P.Nk * P.nb;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
@@ -769,7 +843,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
   const SideArgs<T>& S = P.side[side];
   double2* out = side == 0 ? outR : outL;
   if (out == nullptr) return;
-  const int j = blockIdx.x, kj = j / P.nb;
+  const int j = P.sym ? P.irr[blockIdx.x / P.nb] * P.nb + blockIdx.x % P.nb : blockIdx.x, kj = j / P.nb;
   const size_t NN = G::nn;
   const cplx<T>* ketj = S.ket + (size_t)j * NN;
   const cplx<T>* gketj = S.gket + (size_t)j * 3 * NN;

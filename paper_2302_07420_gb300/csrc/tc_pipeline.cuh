@@ -60,6 +60,15 @@ template <typename T, int N> static Params<T> make_params(tc_ctx* ctx, const dou
   P.hartUs = reinterpret_cast<const T*>(ctx->d_hartUs);
   P.occ = ctx->d_occ;
   P.scratch = reinterpret_cast<cplx<T>*>(ctx->d_scratch);
+  P.sym = ctx->sym;
+  P.nirr = ctx->nirr;
+  P.irr = ctx->d_irr;
+  P.symk = ctx->d_symk;
+  P.symrot = ctx->d_symrot;
+  if constexpr (sizeof(T) == 8) P.symcart = reinterpret_cast<const T*>(ctx->d_symcart64);
+  else P.symcart = reinterpret_cast<const T*>(ctx->d_symcart32);
+  P.star_off = ctx->d_star_off;
+  P.star_k = ctx->d_star_k;
   fill_side<T, N>(ctx, 0, P.side[0]);
   fill_side<T, N>(ctx, 1, P.side[1]);
   return P;
@@ -197,11 +206,17 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   if (need_a4) {
     Params<T> Pa = P;
     Pa.nsmem = smem_vols<T, N>(4);
-    k_occ_pairs<T, N><<<dim3(S.Nk * S.no * P.so, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
+    const int q2_items = P.sym ? P.nirr * S.no : S.Nk * S.no;   // irreducible q2 only with symmetry
+    k_occ_pairs<T, N><<<dim3(q2_items * P.so, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
     TC_CHECK_LAUNCH("k_occ_pairs");
     if (P.so > 1) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 0);
       TC_CHECK_LAUNCH("k_sum_parts");
+      nl[2] += 1;
+    }
+    if (P.sym && P.nirr < S.Nk) {
+      k_unfold<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
+      TC_CHECK_LAUNCH("k_unfold");
       nl[2] += 1;
     }
     k_reduce_a4<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(Pa);
@@ -216,12 +231,13 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   k_prep_zy<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_prep_zy");
   nl[2] += 2;
-  // 4. pair chains
+  // 4. pair chains (with symmetry: output orbitals of irreducible k-points only)
   stage_mark(ctx, st, 3);
+  const int nj_items = P.sym ? P.nirr * S.nb : nj;
   {
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);
-    k_pair_chain<T, N><<<dim3(nj * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
+    k_pair_chain<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
     TC_CHECK_LAUNCH("k_pair_chain");
     stage_mark(ctx, st, 4);
     if (P.sc > 1) {
@@ -231,7 +247,7 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     }
     Params<T> Pb = P;
     Pb.nsmem = smem_vols<T, N>(2);
-    k_pair_3b4<T, N><<<dim3(nj * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
+    k_pair_3b4<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
     TC_CHECK_LAUNCH("k_pair_3b4");
     if (P.sc > 1 && tw[T3B4] != 0) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 2);
@@ -241,8 +257,14 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   }
   // 5. local terms, corrections, back to the sphere
   stage_mark(ctx, st, 5);
-  k_finalize<T, N><<<dim3(nj, nsides), TH, vb1, st>>>(P, outR, outL, ctx->d_box_index);
+  k_finalize<T, N><<<dim3(nj_items, nsides), TH, vb1, st>>>(P, outR, outL, ctx->d_box_index);
   TC_CHECK_LAUNCH("k_finalize");
+  if (P.sym && P.nirr < S.Nk) {
+    // outputs of the other k-points by the same unfolding as the orbitals (the operator commutes with it)
+    const int ru = launch_sym_unfold(ctx, outR, nsides > 1 ? outL : nullptr, st);
+    if (ru != TC_OK) return ru;
+    nl[5] += 1;
+  }
   stage_mark(ctx, st, 6);
   return stage_collect(ctx, 6, nl);
 }

@@ -174,6 +174,30 @@ class Context:
         _lib.check(self.lib, self.h, st)
         return out_phi, out_chi, eig, dim
 
+    def set_symmetry(self, ops, time_reversal=True):
+        """Symmetry-reduced occupied-pair stage (tc_set_symmetry); ops: (nops, 3, 3) integer matrices
+        acting on fractional coordinates, identity included; an empty list switches it off."""
+        ops = np.ascontiguousarray(np.asarray(ops, dtype=np.int32).reshape(-1, 9))
+        st = self.lib.tc_set_symmetry(self.h, ops.shape[0], ops.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      1 if time_reversal else 0)
+        _lib.check(self.lib, self.h, st)
+
+    def symmetry_info(self):
+        """(number of irreducible k-points, (Nk, 6) map {k0, op, tr, K1, K2, K3})."""
+        n = ctypes.c_int()
+        km = np.zeros((self.nk, 6), dtype=np.int32)
+        _lib.check(self.lib, self.h, self.lib.tc_symmetry_info(self.h, ctypes.byref(n),
+                                                               km.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return n.value, km
+
+    def symmetrize_orbitals(self, phi_R, phi_L, stream=None):
+        """In place: orbitals of non-irreducible k-points from their irreducible points (torch or numpy)."""
+        for x in (phi_R, phi_L):
+            self._check_orbitals(x)
+        st = self.lib.tc_symmetrize_orbitals(self.h, _data_ptr(phi_R), _data_ptr(phi_L), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return phi_R, phi_L
+
     def profile(self, enable=True):
         """Enable (and reset) or disable per-stage device timing."""
         _lib.check(self.lib, self.h, self.lib.tc_profile(self.h, 1 if enable else 0))
