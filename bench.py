@@ -52,6 +52,23 @@ def pairs_per_apply(nk, nb, no):
     return 2 * ((nk * nb) * (nk * no) + (nk * no) ** 2)
 
 
+def max_over_ranks(t, dist=None, device=None):
+    """The largest of the ranks' times (t itself without torch.distributed); NCCL reduces on the GPU,
+    gloo on the host."""
+    if dist is None:
+        return t
+    import torch
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world, units_per_step, steps, t):
+    """Whole-job throughput: units of all ranks over the slowest rank's time."""
+    return world * units_per_step * steps / t
+
+
 def kmesh_cart(lattice, kmesh):
     """Cartesian k of the Gamma-centred mesh (fractions in (-1/2, 1/2]) in the library's k order."""
     B = 2.0 * np.pi * np.linalg.inv(np.asarray(lattice)).T
@@ -292,17 +309,13 @@ def run_batch(args):
             bc.apply(d, d, occ, out_r, out_l)
         ev1.record(stream)
         torch.cuda.synchronize()
-    t = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
     npairs = sum(pairs_per_apply(int(np.prod(c["kmesh"])), c["nbands"], c["nocc"]) for c in cells)
     ncell, lanes, lanes_max, tune = bc.info()
     bc.close()
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": world * npairs * args.steps / t, "unit": "pairs/s", "n_gpus": world,
+            "metric": METRIC, "value": job_value(world, npairs, args.steps, t), "unit": "pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "heg_batch: 256 HEG cells, N in {14,38,54,66}, r_s in [1,5], boxes 16^3-32^3, "
@@ -438,12 +451,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     stages = ctx.stage_times()
     ctx.profile(False)
-    t = ms / 1e3
-    if dist is not None:
-        tt = torch.tensor([t], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-    value = world * npairs * args.steps / t
+    t = max_over_ranks(ms / 1e3, dist, dev)
+    value = job_value(world, npairs, args.steps, t)
 
     # dominant kernel (fused pair chains): algorithmic FFT flops / live per-launch time
     pc_ms, pc_launch = stages["pair_chain"]
@@ -493,11 +502,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         ctx.apply_host(h_phi, h_chi, occ)
-    te = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([te], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
+    te = max_over_ranks(time.perf_counter() - t0, dist, dev)
     orb_bytes = c_phi.nbytes
 
     extras = {}
@@ -522,7 +527,7 @@ def main():
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                          "flop_per_launch": flop_per_launch, "ms_per_launch": pc_ms / max(pc_launch, 1),
                          "hbm": hbm},
-            "e2e": {"value": world * npairs * args.steps / te, "unit": "pairs/s",
+            "e2e": {"value": job_value(world, npairs, args.steps, te), "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * orb_bytes + occ.nbytes, "d2h_bytes_per_step": 2 * orb_bytes},
             "gpu_launches": launches,
             "clocks": clk.summary(),
