@@ -87,10 +87,13 @@ template <typename T, int N> __device__ __forceinline__ T pcomp(const PComp<T>& 
 
 template <typename T> __device__ __forceinline__ cplx<T> ld(const cplx<T>* p, size_t i) { return p[i]; }
 
-// Old accumulator value and partner ket of one element, loaded together before a store.
-template <typename T> struct AccKet {
-  cplx<T> acc, ket;
-};
+// *p += v performed in L2 (a reduction without a return value): the SM does not wait
+// for the old value.  Each accumulator element has one owning CTA, and one thread of
+// it adds to the element at a time, so the sums keep their order.
+template <typename T> __device__ __forceinline__ void red_add(cplx<T>* p, cplx<T> v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
 
 template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
               },
               [&](int i, int j, int k, cplx<T> v) { B1[G::sidx(i, j, k)] = v; });
           // old accumulator values, B1 and the partner fields of one element, loaded before any store
-          struct Old3 { cplx<T> h6, a, b, b1, k1, br1; };
+          struct Old3 { cplx<T> b1, k1, br1; };
           inv3d_rmw<T, N, 4>(
               B2,
               [&](int i, int j, int k) {
@@ -360,12 +363,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
               [&](int i, int j, int k) {
                 const int g = G::gidx(i, j, k);
                 Old3 o;
-                o.h6 = H6[g];
                 // the axis-1 pencil of B2 is owned by the thread that wrote the same pencil of B1
                 o.b1 = B1[G::sidx(i, j, k)];
                 if (sp == 0) {
-                  o.a = h3a4[d * NN + g];
-                  o.b = h3b[d * NN + g];
                   o.k1 = ldg(ket1 + g);
                   o.br1 = ldg(bra1 + g);
                 }
@@ -373,10 +373,10 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
               },
               [&](int i, int j, int k, cplx<T> b2, const Old3& o) {
                 const int g = G::gidx(i, j, k);
-                H6[g] = o.h6 + w12 * (o.b1 * b2);
+                red_add(&H6[g], w12 * (o.b1 * b2));
                 if (sp == 0) {
-                  h3a4[d * NN + g] = o.a + f1 * (b2 * o.k1);
-                  h3b[d * NN + g] = o.b + f1 * mulc(o.b1, o.br1);
+                  red_add(&h3a4[d * NN + g], f1 * (b2 * o.k1));
+                  red_add(&h3b[d * NN + g], f1 * mulc(o.b1, o.br1));
                 }
               });
           __syncthreads();
@@ -398,8 +398,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
           return u * FAB[G::sidx(i, j, k)];
         },
         [&](int i, int j, int k, cplx<T> v) {
-          const int g = G::gidx(i, j, k);
-          H6[g] = H6[g] + pref * (v + cF0);
+          red_add(&H6[G::gidx(i, j, k)], pref * (v + cF0));
         });
   }
 }
@@ -653,12 +652,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
         const T fw = -f * tw[T2AX];
         inv3d_rmw<T, N, CH>(
             B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
-            [&](int a, int b, int c) {
-              const int g = G::gidx(a, b, c);
-              return AccKet<T>{acc[g], ldg(ketq + g)};
-            },
-            [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
-              acc[G::gidx(a, b, c)] = o.acc + fw * (o.ket * v);
+            [&](int a, int b, int c) { return ldg(ketq + G::gidx(a, b, c)); },
+            [&](int a, int b, int c, cplx<T> v, const cplx<T>& kq) {
+              red_add(&acc[G::gidx(a, b, c)], fw * (kq * v));
             });
         __syncthreads();
       }
@@ -690,14 +686,6 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
             if (sp == 0) {
 #pragma unroll
               for (int c0 = 0; c0 < N; c0 += CH) {
-                cplx<T> oa[CH], ow[CH];
-#pragma unroll
-                for (int u = 0; u < CH; ++u) {
-                  if (c0 + u >= N) continue;
-                  const int g = G::gidx(c0 + u, i2, i3);
-                  if (need_z) oa[u] = acc[g];
-                  if (need_w) ow[u] = w[d * NN + g];
-                }
                 cplx<T> lz[CH], lk[CH], ly[CH], lb[CH], lj[CH], lh[CH], ln[CH];
 #pragma unroll
                 for (int u = 0; u < CH; ++u) {
@@ -711,8 +699,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
                   if (c0 + u >= N) continue;
                   const int g = G::gidx(c0 + u, i2, i3);
                   const cplx<T> bv = v[c0 + u];
-                  if (need_z) acc[g] = oa[u] + f * (lz[u] * bv);
-                  if (need_w) w[d * NN + g] = ow[u] + f * (lk[u] * bv);
+                  if (need_z) red_add(&acc[g], f * (lz[u] * bv));
+                  if (need_w) red_add(&w[d * NN + g], f * (lk[u] * bv));
                   cplx<T> F = {0, 0};
                   if (need_F) {
                     if (need_y) F = mulc(ly[u], lb[u]);
@@ -751,12 +739,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
       if (need_F || need_ap) {
         inv3d_rmw<T, N, CH>(
             B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
-            [&](int a, int b, int c) {
-              const int g = G::gidx(a, b, c);
-              return AccKet<T>{acc[g], ldg(ketq + g)};
-            },
-            [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
-              acc[G::gidx(a, b, c)] = o.acc + f * (o.ket * v);
+            [&](int a, int b, int c) { return ldg(ketq + G::gidx(a, b, c)); },
+            [&](int a, int b, int c, cplx<T> v, const cplx<T>& kq) {
+              red_add(&acc[G::gidx(a, b, c)], f * (kq * v));
             });
         __syncthreads();
       }
@@ -818,12 +803,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
       const T fw = t3b4 * f;
       inv3d_rmw<T, N, 8>(
           B, [&](int a, int b, int c) { return A[G::sidx(a, b, c)]; },
-          [&](int a, int b, int c) {
-            const int g = G::gidx(a, b, c);
-            return AccKet<T>{acc[g], ldg(ketq + g)};
-          },
-          [&](int a, int b, int c, cplx<T> v, const AccKet<T>& o) {
-            acc[G::gidx(a, b, c)] = o.acc + fw * (o.ket * v);
+          [&](int a, int b, int c) { return ldg(ketq + G::gidx(a, b, c)); },
+          [&](int a, int b, int c, cplx<T> v, const cplx<T>& kq) {
+            red_add(&acc[G::gidx(a, b, c)], fw * (kq * v));
           });
       __syncthreads();
     }
