@@ -195,8 +195,10 @@ tc_status tc_davidson_step(tc_ctx* ctx, const void* phi_R, const void* phi_L, co
  * fractional coordinates).  From then on tc_apply / tc_energy /
  * tc_energy_grad / tc_davidson_step compute the occupied-pair stage
  * (Algs. 4, 6, 8, 11) for irreducible q2 only and obtain the other q2 by
- * rotation, which is exact when the orbitals obey the symmetry (as
- * tc_symmetrize_orbitals makes them); other inputs give undefined results.
+ * rotation, and compute the outputs of irreducible k-points only, the others
+ * following by the same unfolding as the orbitals.  This is exact when the
+ * orbitals obey the symmetry (as tc_symmetrize_orbitals makes them); other
+ * inputs give undefined results.
  * Needs the pair densities to fit the FFT box without wrapping (the Miller
  * span of all spheres, per axis, at most n/2 - 1), else TC_ERR_UNSUPPORTED.
  * nops = 0 switches the reduction off.  Synchronises the device and may

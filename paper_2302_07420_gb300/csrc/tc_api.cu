@@ -529,9 +529,9 @@ int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st) {
   }
   std::memcpy(c->h_occ, occ, nj * sizeof(double));
   cudaError_t e = cudaMemcpyAsync(c->d_occ, c->h_occ, nj * sizeof(double), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaEventRecord(c->occ_ev, st);
+  if (e == cudaSuccess && c->occ_ev) e = cudaEventRecord(c->occ_ev, st);
   if (e != cudaSuccess) return cuda_fail(c, e, "occ upload");
-  c->occ_pending = true;
+  c->occ_pending = c->occ_ev != nullptr;
   return TC_OK;
 }
 
