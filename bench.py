@@ -33,8 +33,8 @@ FFTS_PER_PAIR_CHAIN = 15   # k_pair_chain: rho, V, 3 pp inverse, 3 pp forward, 3
 # DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload, from one 1-pass capture:
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:k_pair_chain -s 3 -c 1 python bench.py --profile-run --steps 1 --warmup 3
-# (150.64 GB read + 75.64 GB written).  Reset to None whenever k_pair_chain changes.
-CHAIN_TRAFFIC_BYTES = 150.64e9 + 75.64e9
+# (123.18 GB read + 68.04 GB written).  Reset to None whenever k_pair_chain changes.
+CHAIN_TRAFFIC_BYTES = 123.18e9 + 68.04e9
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
 
