@@ -485,6 +485,10 @@ def main():
     ms64 = e0.elapsed_time(e1) / args.fp64_steps
     ref_scale = max(float(r64.abs().max()), float(l64.abs().max()))
     err32 = max(float((out_r - r64).abs().max()), float((out_l - l64).abs().max())) / ref_scale
+    # total energy per cell (Eqs. EtotTC / EtotBiTC): FP32 path against the FP64 path, per electron
+    e64 = ctx64.energy(d_phi, d_chi, occ)
+    e32 = ctx.energy(d_phi, d_chi, occ)
+    err_e = abs(e32 - e64) / p["nelec"]
     ctx64.close()
     err_oracle = None
     gpath = os.path.join(ROOT, "tests", "golden", "si_k444.json")
@@ -533,7 +537,8 @@ def main():
             "clocks": clk.summary(),
             "fp64": {"value": npairs / (ms64 / 1e3), "unit": "pairs/s", "ms_per_step": ms64,
                      "steps": args.fp64_steps},
-            "error": {"fp32_vs_fp64_gpu_max_rel": err32, "fp64_gpu_vs_oracle_sampled_max_rel": err_oracle},
+            "error": {"fp32_vs_fp64_gpu_max_rel": err32, "fp64_gpu_vs_oracle_sampled_max_rel": err_oracle,
+                      "energy_fp32_vs_fp64_ha_per_electron": err_e, "energy_fp64_ha_per_cell": e64},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,
         }
