@@ -167,10 +167,10 @@ class TCOperator:
         nt = bk.FT(n)
         self.nt = nt
         self.vH = bk.iFT(Vh * nt)                                     # Alg. 1
-        self.h1 = bk.iFT(Uh * nt[None])                               # Alg. 3 line 1-2
+        self.h1 = bk.iFT(Uh * nt[None])                               # Alg. 3 (h1)
         mt = bk.FT(m)
         self.vb2 = bk.iFT(np.sum(-Uh * mt, axis=0))
-        h1n = bk.FT(bk.mul(self.h1, n[None]))                         # Alg. 7 lines 3-4
+        h1n = bk.FT(bk.mul(self.h1, n[None]))                         # Alg. 7
         self.t3b1 = bk.iFT(np.sum(-Uh * h1n, axis=0))
         self._occupied_pairs()
         self._prepared = True
@@ -200,10 +200,10 @@ class TCOperator:
                     c6[k2] = c6[k2] + np.sum(w[:, :, None, None, None] * prod, axis=(0, 1))
                     if s == 0:
                         f1 = self.f[k1] / Nk
-                        # h3(q2) += f1 P^pp(q1,q2) phi_q1            (Alg. 6 line 8)
+                        # h3(q2) += f1 P^pp(q1,q2) phi_q1            (Alg. 6)
                         t = bk.mul(PB, self.ket[k1][:no][:, None, None])
                         h3a4[k2] = h3a4[k2] + np.sum(f1[:, None, None, None, None, None] * t, axis=0)
-                        # h3b(q2) += f1 P^pp(q2,q1) chi_q1^*         (Alg. 8 line 7)
+                        # h3b(q2) += f1 P^pp(q2,q1) chi_q1^*         (Alg. 8)
                         t = bk.mul(PA, bk.conj(self.bra[k1][:no])[None, :, None])
                         h3b[k2] = h3b[k2] + np.sum(f1[None, :, None, None, None, None] * t, axis=1)
         if S.div_correction:

@@ -198,9 +198,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
     a = S.n; dst = S.nt;
   } else if (which == 1) {   // m~_c
     a = S.m + (size_t)c * G::nn; dst = S.mt + (size_t)c * G::nn;
-  } else if (which == 2) {   // FT[h1_c n]  (Alg. 7 line 4)
+  } else if (which == 2) {   // FT[h1_c n]  (Alg. 7)
     a = S.h1 + (size_t)c * G::nn; b = S.n; dst = S.spec + (size_t)c * G::nn;
-  } else {                   // FT[h5_c]    (Alg. 8 line 16)
+  } else {                   // FT[h5_c]    (Alg. 8)
     a = S.h5 + (size_t)c * G::nn; dst = S.spec + (size_t)c * G::nn;
   }
   fwd3d<T, N>(
@@ -414,7 +414,7 @@ template <int N> __device__ __forceinline__ int sym_image(const int* R, int i1, 
   return (y[0] * N + y[1]) * N + y[2];
 }
 
-// h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8 lines 9-10).
+// h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8).
 // With symmetry the part of an irreducible q2;0 stands for every q2 of its star:
 // part(q2)(x) = part(q2;0)(S x), conjugated under time reversal (Sec. 2.6.4).
 template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
