@@ -30,11 +30,12 @@ METRIC = "TC-operator orbital-pair convolutions/sec and % HBM roofline, FP32 vs 
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # derived ALU peak (FMA = 2 flop)
 FFTS_PER_PAIR_CHAIN = 15   # k_pair_chain: rho, V, 3 pp inverse, 3 pp forward, 3 ap inverse, 3 ap forward, final
-# DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload, from one 1-pass capture:
+# DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload with the autotuned
+# partner-chunk count (4), from one 1-pass capture (the autotuner's 9 applies and 3 warm-ups are skipped):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
-#       -k regex:k_pair_chain -s 3 -c 1 python bench.py --profile-run --steps 1 --warmup 3
-# (123.18 GB read + 68.04 GB written).  Reset to None whenever k_pair_chain changes.
-CHAIN_TRAFFIC_BYTES = 123.18e9 + 68.04e9
+#       -k regex:k_pair_chain -s 12 -c 1 python bench.py --profile-run --steps 1 --warmup 3
+# (74.32 GB read + 58.08 GB written).  Reset to None whenever k_pair_chain or its launch changes.
+CHAIN_TRAFFIC_BYTES = 74.32e9 + 58.08e9
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
 
@@ -413,6 +414,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    # partner-chunk counts of the two-sided apply measured on this workload (setup, outside the timed region)
+    so_sc = ctx.autotune(d_phi, d_chi, occ)
     if args.profile_davidson:
         for _ in range(args.warmup + args.steps):
             ctx.davidson_step(d_phi, d_chi, occ)
@@ -525,6 +528,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "pairs_per_step": npairs, "precision": "fp32 FFTs and pair products",
                        "l2": "no flush: the fields touched per step (~1 GB) exceed the 129 MB L2",
+                       "partner_chunks": {"occ_pairs": so_sc[0], "pair_chain": so_sc[1], "chosen_by": "tc_autotune"},
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_pair_chain",

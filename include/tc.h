@@ -230,6 +230,17 @@ tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* 
  * accumulate until tc_profile(ctx, 1) is called again. */
 enum { TC_NSTAGES = 6 };
 tc_status tc_profile(tc_ctx* ctx, int enable);
+/* Autotuner of the partner-chunk counts of the two-sided apply: runs the
+ * operator on the given inputs once per candidate count s = 1 .. min(8,
+ * Nk nocc) (after one warm-up) and keeps, separately, the s with the shortest
+ * device time of the occupied-pair stage (so_out) and of the pair-chain and
+ * 3b4 stages (sc_out); later two-sided calls use them (one-sided calls keep
+ * the counts chosen from the SM count).  The chunk count changes only the
+ * order of partial sums (results agree to rounding).  Orbital arrays host or
+ * device, occ host; resets the per-stage times; re-allocates the workspace;
+ * blocks the host.  Not for batch contexts (TC_ERR_STATE). */
+tc_status tc_autotune(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, int* so_out,
+                      int* sc_out, void* cuda_stream);
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
 tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
 

@@ -198,6 +198,17 @@ class Context:
         _lib.check(self.lib, self.h, st)
         return phi_R, phi_L
 
+    def autotune(self, phi_R, phi_L, occ, stream=None):
+        """Measure and keep the partner-chunk counts of the two-sided apply (tc_autotune): (so, sc)."""
+        for x in (phi_R, phi_L):
+            self._check_orbitals(x)
+        occ_np, occ_p = self._occ(occ)
+        so, sc = ctypes.c_int(), ctypes.c_int()
+        st = self.lib.tc_autotune(self.h, _data_ptr(phi_R), _data_ptr(phi_L), occ_p, ctypes.byref(so),
+                                  ctypes.byref(sc), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return so.value, sc.value
+
     def profile(self, enable=True):
         """Enable (and reset) or disable per-stage device timing."""
         _lib.check(self.lib, self.h, self.lib.tc_profile(self.h, 1 if enable else 0))

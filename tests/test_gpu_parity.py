@@ -199,3 +199,22 @@ def test_repeated_calls_in_one_context_are_identical(prec):
     for a, b in zip(outs[0::2], outs[1::2]):
         assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
     assert np.array_equal(outs[0][1], outs[4][1])
+
+
+def test_autotune_keeps_the_operator():
+    """tc_autotune only reorders partial sums: the outputs before and after agree to FP64 rounding, and
+    the chosen chunk counts lie in [1, min(8, Nk nocc)]."""
+    p, S, c_phi, c_chi, occ = tiny_case(1, (2, 1, 1), 12)
+    ctx = _ctx(p)
+    try:
+        r0, l0 = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+        r0, l0 = r0.cpu().numpy(), l0.cpu().numpy()
+        so, sc = ctx.autotune(_dev(c_phi), _dev(c_chi), occ)
+        r1, l1 = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+        r1, l1 = r1.cpu().numpy(), l1.cpu().numpy()
+    finally:
+        ctx.close()
+    top = min(8, S.Nk * S.nocc)
+    assert 1 <= so <= top and 1 <= sc <= top
+    sc_ = np.abs(r0).max()
+    assert np.abs(r1 - r0).max() < 1e-13 * sc_ and np.abs(l1 - l0).max() < 1e-13 * sc_
