@@ -230,15 +230,16 @@ tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* 
  * accumulate until tc_profile(ctx, 1) is called again. */
 enum { TC_NSTAGES = 6 };
 tc_status tc_profile(tc_ctx* ctx, int enable);
-/* Autotuner of the partner-chunk counts of the two-sided apply: runs the
- * operator on the given inputs once per candidate count s = 1 .. min(8,
- * Nk nocc) (after one warm-up) and keeps, separately, the s with the shortest
- * device time of the occupied-pair stage (so_out) and of the pair-chain and
- * 3b4 stages (sc_out); later two-sided calls use them (one-sided calls keep
- * the counts chosen from the SM count).  The chunk count changes only the
- * order of partial sums (results agree to rounding).  Orbital arrays host or
- * device, occ host; resets the per-stage times; re-allocates the workspace;
- * blocks the host.  Not for batch contexts (TC_ERR_STATE). */
+/* Autotuner of the partner-chunk counts: runs the operator on the given
+ * inputs once per candidate count s = 1 .. min(8, Nk nocc) (after one
+ * warm-up), for two-sided launches (tc_apply, tc_energy_grad) and then for
+ * one-sided ones (tc_energy, tc_davidson_step), and keeps, separately for
+ * each, the s with the shortest device time of the occupied-pair stage and of
+ * the pair-chain and 3b4 stages; so_out / sc_out return the two-sided
+ * choices.  The chunk count changes only the order of partial sums (results
+ * agree to rounding).  Orbital arrays host or device, occ host; resets the
+ * per-stage times; re-allocates the workspace; blocks the host.  Not for
+ * batch contexts (TC_ERR_STATE). */
 tc_status tc_autotune(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, int* so_out,
                       int* sc_out, void* cuda_stream);
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */

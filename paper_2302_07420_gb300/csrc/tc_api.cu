@@ -890,7 +890,6 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
   const tc::Setup& S = c->S;
   const int M = S.Nk * S.no;
   const int smax = std::min(8, M);
-  const int keep_occ0 = c->split_occ[0], keep_chain0 = c->split_chain[0];
   const bool prof_was = c->profile;
   // workspace for the largest candidate
   c->so_max = std::max(c->so_max, smax);
@@ -902,33 +901,36 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
   double tw[NT];
   term_weights(c, tw, 1.0, 1.0);
   bool host_out = false;
-  double best_occ = 1e300, best_chain = 1e300;
-  int so = 1, sc = 1;
-  for (int s = 0; s <= smax; ++s) {
-    // s = 0 is an untimed warm-up with one chunk; then one measured apply per candidate
-    const int cand = s == 0 ? 1 : s;
-    c->split_occ[1] = cand;
-    c->split_chain[1] = cand;
-    for (int i = 0; i < 8; ++i) c->stage_ms[i] = 0.0;
-    rs = run_common(c, phi, chi, occ, c->d_out_R, c->d_out_L, tw, 2, st, &host_out);
-    if (rs != TC_OK) break;
-    if (s == 0) continue;
-    const double t_occ = c->stage_ms[2], t_chain = c->stage_ms[3] + c->stage_ms[4];
-    if (t_occ < best_occ) { best_occ = t_occ; so = cand; }
-    if (t_chain < best_chain) { best_chain = t_chain; sc = cand; }
+  int so[2] = {c->split_occ[0], c->split_occ[1]}, sc[2] = {c->split_chain[0], c->split_chain[1]};
+  // two-sided launches (tc_apply, tc_energy_grad), then one-sided ones (tc_energy, tc_davidson_step)
+  for (int nsides = 2; nsides >= 1 && rs == TC_OK; --nsides) {
+    double best_occ = 1e300, best_chain = 1e300;
+    for (int s = 0; s <= smax; ++s) {
+      // s = 0 is an untimed warm-up with one chunk; then one measured apply per candidate
+      const int cand = s == 0 ? 1 : s;
+      c->split_occ[nsides - 1] = cand;
+      c->split_chain[nsides - 1] = cand;
+      for (int i = 0; i < 8; ++i) c->stage_ms[i] = 0.0;
+      rs = run_common(c, phi, chi, occ, c->d_out_R, nsides == 2 ? c->d_out_L : nullptr, tw, nsides, st, &host_out);
+      if (rs != TC_OK) break;
+      if (s == 0) continue;
+      const double t_occ = c->stage_ms[2], t_chain = c->stage_ms[3] + c->stage_ms[4];
+      if (t_occ < best_occ) { best_occ = t_occ; so[nsides - 1] = cand; }
+      if (t_chain < best_chain) { best_chain = t_chain; sc[nsides - 1] = cand; }
+    }
   }
   tc_profile(c, prof_was ? 1 : 0);
-  if (rs != TC_OK) return rs;
-  c->split_occ[0] = keep_occ0;
-  c->split_chain[0] = keep_chain0;
-  c->split_occ[1] = so;
-  c->split_chain[1] = sc;
-  c->so_max = std::max(keep_occ0, so);
-  c->sc_max = std::max(keep_chain0, sc);
+  c->split_occ[0] = so[0];
+  c->split_occ[1] = so[1];
+  c->split_chain[0] = sc[0];
+  c->split_chain[1] = sc[1];
+  c->so_max = std::max(so[0], so[1]);
+  c->sc_max = std::max(sc[0], sc[1]);
   r = tc::rebuild_workspace(c);
+  if (rs != TC_OK) return rs;
   if (r != TC_OK) return (tc_status)r;
-  if (so_out) *so_out = so;
-  if (sc_out) *sc_out = sc;
+  if (so_out) *so_out = so[1];
+  if (sc_out) *sc_out = sc[1];
   return TC_OK;
 }
 
