@@ -182,3 +182,22 @@ def test_davidson_step_silicon_like_2x2x2():
     ref = DV.davidson_step(S, c_phi, c_chi, occ)
     got = _run(p, c_phi, c_chi, occ)
     _compare(S, ref, got, 1e-11, 1e-9)
+
+
+@pytest.mark.parametrize("ecut,scale", [(4.0, 7.0), (5.0, 5.0)])
+def test_davidson_step_many_bands_global_solver(ecut, scale):
+    """40 bands: the subspace arrays (2 d^2 + 4 m d complex words for d up to 80) exceed shared memory,
+    so the eigen-solver runs on global scratch; d = 80 (every new vector kept) and d = 59 (the sphere has
+    59 plane waves: the space is exhausted and the step is exact)."""
+    m = 40
+    p = synth.tiny_params(11, kmesh=(1, 1, 1), fft=(18, 18, 18) if scale > 6 else (16, 16, 16), ecut=ecut,
+                          nbands=m, nocc=2, scale=scale)
+    S = make_setup(p)
+    c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 730, [S.kpG(k) for k in range(S.Nk)], S.npw_max, m,
+                                         perturb=0.1)
+    occ = np.zeros((S.Nk, m))
+    occ[:, :2] = [1.0, 0.8]
+    ref = DV.davidson_step(S, c_phi, c_chi, occ)
+    got = _run(p, c_phi, c_chi, occ)
+    assert got[3][0] == min(2 * m, S.npw[0])
+    _compare(S, ref, got, 1e-11, 1e-8)
