@@ -71,6 +71,10 @@ struct tc_ctx {
   int* d_sym_src = nullptr;        // [Nk][npw_max] sphere index at k0 of each coefficient at k (-1 pad)
   double* d_symcart64 = nullptr;   // [nops][9]
   float* d_symcart32 = nullptr;
+  // when set for one launch: a context with the same partners (occupied bands, occupations, cell,
+  // precision) whose last launch left its partner-only fields (densities, Hartree-type fields,
+  // occupied-pair stage) for the same sides; they are copied instead of recomputed
+  const tc_ctx* partners_from = nullptr;
   // the last occupation upload from h_occ (h_occ is rewritten only after it has run)
   cudaEvent_t occ_ev = nullptr;
   bool occ_pending = false;

@@ -724,7 +724,11 @@ tc_status tc_davidson_step(tc_ctx* c, const void* phi, const void* chi, const do
     for (int b = 0; b < na; ++b) D->occ_aux[k * na + b] = b < no ? occ[k * m + b] : 0.0;
   rr = tc::stage_occ(D->aux, D->occ_aux.data(), st);
   if (rr != TC_OK) return dav_fail(c, (tc_status)rr, D->aux->err);
+  // same partners as the h v launch: its partner-only fields (densities, Hartree-type fields, the
+  // occupied-pair stage) are copied rather than recomputed
+  D->aux->partners_from = c;
   rr = tc::apply_sides(D->aux, D->aux_phi, D->aux_chi, D->hw, nullptr, 1, st);
+  D->aux->partners_from = nullptr;
   if (rr != TC_OK) return dav_fail(c, (tc_status)rr, D->aux->err);
   // 4. subspace eigenpairs
   const size_t eig_smem = D->eig_in_smem ? D->eig_words * sizeof(double2) : 0;

@@ -185,6 +185,31 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
                                                    (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi,
                                                    (cplx<T>*)ctx->d_scratch);
   TC_CHECK_LAUNCH("k_orbitals");
+  const tc_ctx* src = ctx->partners_from;
+  if (src) {
+    // stages 2 and 3 up to the local potential from a context with the same partners: the 25
+    // base fields of each side (n .. vloc, contiguous) and part 0 of both occupied-pair h3 kinds
+    stage_mark(ctx, st, 1);
+    const size_t vb_el = sizeof(cplx<T>) * (size_t)S.N;
+    for (int sd = 0; sd < nsides; ++sd) {
+      SideArgs<T> from{};
+      fill_side<T, N>(const_cast<tc_ctx*>(src), sd, from);
+      cudaError_t e = cudaMemcpyAsync(P.side[sd].n, from.n, 25 * vb_el, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.side[sd].h3a4, from.h3a4, (size_t)S.Nk * S.no * 3 * vb_el, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.side[sd].h3b, from.h3b, (size_t)S.Nk * S.no * 3 * vb_el, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        ctx->err = std::string("partner fields: ") + cudaGetErrorString(e);
+        return TC_ERR_CUDA;
+      }
+    }
+    nl[1] = 0;
+    nl[2] = 1;
+    stage_mark(ctx, st, 2);
+    k_prep_zy<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
+    TC_CHECK_LAUNCH("k_prep_zy");
+  } else {
   // 2. densities and Hartree-type fields
   stage_mark(ctx, st, 1);
   k_density<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
@@ -231,6 +256,7 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   k_prep_zy<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_prep_zy");
   nl[2] += 2;
+  }
   // 4. pair chains (with symmetry: output orbitals of irreducible k-points only)
   stage_mark(ctx, st, 3);
   const int nj_items = P.sym ? P.nirr * S.nb : nj;
