@@ -421,6 +421,24 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
     return why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
   }
   tc::Setup& S = c->S;
+  {
+    // the left/right conjugation of the occupied-pair fields holds on the grid for odd boxes, or
+    // when no pair density reaches the Nyquist plane (Miller span of all spheres <= n/2 - 1)
+    bool clear = S.n % 2 == 1;
+    if (!clear) {
+      clear = true;
+      for (int i = 0; i < 3; ++i) {
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int k = 0; k < S.Nk; ++k)
+          for (int g = 0; g < S.npw[k]; ++g) {
+            lo = std::min(lo, S.miller[k][g][i]);
+            hi = std::max(hi, S.miller[k][g][i]);
+          }
+        if (hi - lo > S.n / 2 - 1) clear = false;
+      }
+    }
+    c->left_from_right = clear;
+  }
   c->prec = params->precision;
   c->esz = c->prec == TC_FP64 ? 16 : 8;
   c->ws_owned = own_workspace;
@@ -929,7 +947,8 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
   r = tc::rebuild_workspace(c);
   if (rs != TC_OK) return rs;
   if (r != TC_OK) return (tc_status)r;
-  if (so_out) *so_out = so[1];
+  // two-sided launches that derive the left side run the occupied-pair stage one-sided
+  if (so_out) *so_out = c->left_from_right ? so[0] : so[1];
   if (sc_out) *sc_out = sc[1];
   return TC_OK;
 }

@@ -71,6 +71,9 @@ struct tc_ctx {
   int* d_sym_src = nullptr;        // [Nk][npw_max] sphere index at k0 of each coefficient at k (-1 pad)
   double* d_symcart64 = nullptr;   // [nops][9]
   float* d_symcart32 = nullptr;
+  // two-sided launches derive the left occupied-pair fields from the right ones (exact here:
+  // odd box, or pair densities clear of the Nyquist planes)
+  bool left_from_right = false;
   // when set for one launch: a context with the same partners (occupied bands, occupations, cell,
   // precision) whose last launch left its partner-only fields (densities, Hartree-type fields,
   // occupied-pair stage) for the same sides; they are copied instead of recomputed

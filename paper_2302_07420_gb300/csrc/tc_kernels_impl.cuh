@@ -417,16 +417,17 @@ template <int N> __device__ __forceinline__ int sym_image(const int* R, int i1, 
 // h6 = sum over CTAs of the parts; h5_d = sum_q2 f/Nk h3b(q2)_d ket_q2 (Alg. 8).
 // With symmetry the part of an irreducible q2;0 stands for every q2 of its star:
 // part(q2)(x) = part(q2;0)(S x), conjugated under time reversal (Sec. 2.6.4).
-template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
+template <typename T, int N> __global__ void k_reduce_a4(Params<T> P, int side0, int h5_only) {
   using G = Geo<N>;
   constexpr int NS = 6;
-  const int side = blockIdx.y;
+  const int side = side0 + blockIdx.y;
   const SideArgs<T>& S = P.side[side];
   const size_t NN = G::nn;
   const int M = P.Nk * P.no, ncta = (P.sym ? P.nirr * P.no : M) * P.so;   // k_occ_pairs CTAs per side
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < (int)NN; r += gridDim.x * blockDim.x) {
     cplx<T> h6 = {0, 0}, h5[3] = {{0, 0}, {0, 0}, {0, 0}};
-    if (!P.sym) {
+    if (h5_only) {
+    } else if (!P.sym) {
       for (int c = 0; c < ncta; ++c) {
         const size_t cta = (size_t)side * ncta + c;
         h6 = h6 + P.scratch[(cta * NS + 4) * (size_t)Geo<N>::vol + r];
@@ -452,9 +453,30 @@ template <typename T, int N> __global__ void k_reduce_a4(Params<T> P) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) h5[d] = h5[d] + f * (S.h3b[((size_t)c * 3 + d) * NN + r] * kv);
     }
-    S.h6[r] = h6;
+    if (!h5_only) S.h6[r] = h6;
 #pragma unroll
     for (int d = 0; d < 3; ++d) S.h5[d * NN + r] = h5[d];
+  }
+}
+
+// Left-side occupied-pair fields from the right side's.  With F = FT of a pair density and
+// U(p) = i p u~(p) (so conj U(p) = U(-p)), the left pair field of (a, b) is the conjugate of the
+// right one of (b, a), P_L(a, b) = conj P_R(b, a); summed as in the occupied-pair stage this
+// gives h6_L = conj h6_R, h3(3a4)_L = conj h3(3b)_R and h3(3b)_L = conj h3(3a4)_R.  Exact on the
+// grid when -m is the negated Miller vector of every box index a pair density occupies (odd n,
+// or pair densities that do not reach the Nyquist planes); the pipeline uses it only then.
+template <typename T, int N> __global__ void k_left_from_right(Params<T> P) {
+  const SideArgs<T>& R = P.side[0];
+  const SideArgs<T>& L = P.side[1];
+  const size_t NN = (size_t)N * N * N, M3 = (size_t)P.Nk * P.no * 3 * NN;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < NN + M3; e += (size_t)gridDim.x * blockDim.x) {
+    if (e < NN) {
+      L.h6[e] = conjg(R.h6[e]);
+    } else {
+      const size_t i = e - NN;
+      L.h3a4[i] = conjg(R.h3b[i]);
+      L.h3b[i] = conjg(R.h3a4[i]);
+    }
   }
 }
 

@@ -229,23 +229,35 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   stage_mark(ctx, st, 2);
   const bool need_a4 = tw[T3A2] != 0 || tw[T3A4] != 0 || tw[T3B2] != 0 || tw[T3B5] != 0;
   if (need_a4) {
+    // two-sided launches compute the right side only and conjugate it into the left one when
+    // that is exact on this grid (see k_left_from_right)
+    const bool derive_left = nsides == 2 && ctx->left_from_right;
+    const int occ_sides = derive_left ? 1 : nsides;
     Params<T> Pa = P;
     Pa.nsmem = smem_vols<T, N>(4);
+    if (derive_left) Pa.so = ctx->split_occ[0];
     const int q2_items = P.sym ? P.nirr * S.no : S.Nk * S.no;   // irreducible q2 only with symmetry
-    k_occ_pairs<T, N><<<dim3(q2_items * P.so, nsides), TH, Pa.nsmem * vb, st>>>(Pa);
+    k_occ_pairs<T, N><<<dim3(q2_items * Pa.so, occ_sides), TH, Pa.nsmem * vb, st>>>(Pa);
     TC_CHECK_LAUNCH("k_occ_pairs");
-    if (P.so > 1) {
-      k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 0);
+    if (Pa.so > 1) {
+      k_sum_parts<T, N><<<dim3(2 * pw_blocks, occ_sides), 256, 0, st>>>(Pa, 0);
       TC_CHECK_LAUNCH("k_sum_parts");
       nl[2] += 1;
     }
     if (P.sym && P.nirr < S.Nk) {
-      k_unfold<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
+      k_unfold<T, N><<<dim3(2 * pw_blocks, occ_sides), 256, 0, st>>>(P);
       TC_CHECK_LAUNCH("k_unfold");
       nl[2] += 1;
     }
-    k_reduce_a4<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(Pa);
+    k_reduce_a4<T, N><<<dim3(pw_blocks, occ_sides), 256, 0, st>>>(Pa, 0, 0);
     TC_CHECK_LAUNCH("k_reduce_a4");
+    if (derive_left) {
+      k_left_from_right<T, N><<<2 * pw_blocks, 256, 0, st>>>(P);
+      TC_CHECK_LAUNCH("k_left_from_right");
+      k_reduce_a4<T, N><<<dim3(pw_blocks, 1), 256, 0, st>>>(Pa, 1, 1);   // h5 of the left side
+      TC_CHECK_LAUNCH("k_reduce_a4");
+      nl[2] += 2;
+    }
     k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 3);
     k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 4);
     TC_CHECK_LAUNCH("hartree 3b2");

@@ -168,3 +168,32 @@ def test_partners_enter_only_through_the_density_matrix():
     for half in (slice(0, 2), slice(2, 4)):
         np.testing.assert_allclose(r2[:, half], r1, rtol=0, atol=1e-13 * scale)
         np.testing.assert_allclose(l2[:, half], l1, rtol=0, atol=1e-13 * scale)
+
+
+@pytest.mark.parametrize("fft,ecut,exact", [((9, 9, 9), 1.6, True), ((12, 12, 12), 1.6, True),
+                                            ((12, 12, 12), 6.0, False)])
+def test_left_occupied_pair_fields_are_conjugates_of_the_right(fft, ecut, exact):
+    """P_L(a, b) = conj P_R(b, a) (conj U(p) = U(-p) for U = i p u~): h6_L = conj h6_R and the two h3
+    kinds swap under conjugation.  Exact on the grid for odd boxes and for pair densities clear of the
+    Nyquist planes; an even box whose pair densities wrap onto them breaks it (the library then
+    computes both sides)."""
+    from paper_2302_07420_gb300 import synth as SY
+    p = SY.tiny_params(3, kmesh=(1, 1, 2), fft=fft, ecut=ecut, nbands=3, nocc=2, scale=5.0)
+    S = make_setup(p)
+    c_phi, c_chi = SY.random_orbitals(SY.SEED0 + 903, [S.kpG(k) for k in range(S.Nk)], S.npw_max, 3,
+                                      perturb=0.1)
+    occ = np.zeros((S.Nk, 3))
+    occ[:, :2] = [1.0, 0.7]
+    R = OP.TCOperator(S, c_phi, c_chi, occ, left=False)
+    L = OP.TCOperator(S, c_phi, c_chi, occ, left=True)
+    R.prepare()
+    L.prepare()
+    err = max(np.abs(L.h6 - np.conj(R.h6)).max() / np.abs(R.h6).max(),
+              max(np.abs(L.h3a4[k] - np.conj(R.h3b[k])).max() for k in range(S.Nk)) /
+              max(np.abs(R.h3b[k]).max() for k in range(S.Nk)),
+              max(np.abs(L.h3b[k] - np.conj(R.h3a4[k])).max() for k in range(S.Nk)) /
+              max(np.abs(R.h3a4[k]).max() for k in range(S.Nk)))
+    if exact:
+        assert err < 1e-14
+    else:
+        assert err > 1e-9
