@@ -669,17 +669,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
         }
         __syncthreads();
       }
-      // 2ax
-      if (tw[T2AX] != T(0)) {
-        const T fw = -f * tw[T2AX];
-        inv3d_rmw<T, N, CH>(
-            B, [&](int a, int b, int c) { return Vt[G::gidx(a, b, c)] * A[G::sidx(a, b, c)]; },
-            [&](int a, int b, int c) { return ldg(ketq + G::gidx(a, b, c)); },
-            [&](int a, int b, int c, cplx<T> v, const cplx<T>& kq) {
-              red_add(&acc[G::gidx(a, b, c)], fw * (kq * v));
-            });
-        __syncthreads();
-      }
+      // (2ax, -f ket_q FT^{-1}[V A], shares the final inverse transform: acc += f ket_q FT^{-1}[C - V A])
+      const T t2ax = tw[T2AX];
       // grad-u channels: pp (with the fused second-stage vector field) and ap (3b6)
       for (int sp = 0; sp < 2; ++sp) {
         if (sp == 0 && !(need_pp || need_F)) continue;
@@ -758,9 +749,16 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
           __syncthreads();
         }
       }
-      if (need_F || need_ap) {
+      const bool has_C = need_F || need_ap;
+      if (has_C || t2ax != T(0)) {
         inv3d_rmw<T, N, CH>(
-            B, [&](int a, int b, int c) { return C[G::sidx(a, b, c)]; },
+            B,
+            [&](int a, int b, int c) {
+              const int s = G::sidx(a, b, c);
+              cplx<T> v = has_C ? C[s] : cplx<T>{0, 0};
+              if (t2ax != T(0)) v = v - (t2ax * Vt[G::gidx(a, b, c)]) * A[s];
+              return v;
+            },
             [&](int a, int b, int c) { return ldg(ketq + G::gidx(a, b, c)); },
             [&](int a, int b, int c, cplx<T> v, const cplx<T>& kq) {
               red_add(&acc[G::gidx(a, b, c)], f * (kq * v));
