@@ -30,14 +30,13 @@ METRIC = "TC-operator orbital-pair convolutions/sec and % HBM roofline, FP32 vs 
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # derived ALU peak (FMA = 2 flop)
 FFTS_PER_PAIR_CHAIN = 14   # k_pair_chain: rho, 3 pp inverse, 3 pp forward, 3 ap inverse, 3 ap forward, final (with V)
-# DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload with the autotuned
-# partner-chunk count (4), from one 1-pass capture (the autotuner's 18 applies and 3 warm-ups skipped):
+# DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload, by the partner-chunk
+# count the autotuner chose, each from one 1-pass capture (the autotuner's 18 applies and 3 warm-ups skipped):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none \
 #       -k regex:k_pair_chain -s 21 -c 1 python bench.py --profile-run --steps 1 --warmup 3
-# (74.58 GB read + 58.51 GB written).  Reported only when the launch has that chunk count; reset to None
-# whenever k_pair_chain changes.
-CHAIN_TRAFFIC_BYTES = None
-CHAIN_TRAFFIC_CHUNKS = 4
+# 2 chunks: 81.53 GB read + 58.41 GB written; 4 chunks: 81.77 + 60.86 GB.  Reported only for a captured chunk
+# count; cleared whenever k_pair_chain changes.
+CHAIN_TRAFFIC = {2: 81.53e9 + 58.41e9, 4: 81.77e9 + 60.86e9}
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
 
@@ -472,8 +471,7 @@ def main():
     achieved = flop_per_launch / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e12
     launches = sum(v[1] for v in stages.values())
     # HBM view of the same launch: measured DRAM bytes / live launch time, against the measured copy peak
-    traffic = (CHAIN_TRAFFIC_BYTES if CHAIN_TRAFFIC_BYTES and args.workload == "si_k444"
-               and so_sc[1] == CHAIN_TRAFFIC_CHUNKS else None)
+    traffic = CHAIN_TRAFFIC.get(so_sc[1]) if args.workload == "si_k444" else None
     hbm = None
     if traffic is not None:
         gbps = traffic / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9

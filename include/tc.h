@@ -234,9 +234,9 @@ tc_status tc_profile(tc_ctx* ctx, int enable);
  * inputs once per candidate count s = 1 .. min(8, Nk nocc) (after one
  * warm-up), for two-sided launches (tc_apply, tc_energy_grad) and then for
  * one-sided ones (tc_energy, tc_davidson_step), and keeps, separately for
- * each, the s with the shortest device time of the occupied-pair stage and of
- * the pair-chain and 3b4 stages; so_out / sc_out return the two-sided
- * choices.  The chunk count changes only the order of partial sums (results
+ * each, the smallest s whose device time is within 2 % of the shortest for
+ * the occupied-pair stage and for the pair-chain and 3b4 stages; so_out /
+ * sc_out return the two-sided choices.  The chunk count changes only the order of partial sums (results
  * agree to rounding).  Orbital arrays host or device, occ host; resets the
  * per-stage times; re-allocates the workspace; blocks the host.  Not for
  * batch contexts (TC_ERR_STATE). */

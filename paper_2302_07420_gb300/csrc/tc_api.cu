@@ -922,7 +922,7 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
   int so[2] = {c->split_occ[0], c->split_occ[1]}, sc[2] = {c->split_chain[0], c->split_chain[1]};
   // two-sided launches (tc_apply, tc_energy_grad), then one-sided ones (tc_energy, tc_davidson_step)
   for (int nsides = 2; nsides >= 1 && rs == TC_OK; --nsides) {
-    double best_occ = 1e300, best_chain = 1e300;
+    double t_occ[9] = {}, t_chain[9] = {};
     for (int s = 0; s <= smax; ++s) {
       // s = 0 is an untimed warm-up with one chunk; then one measured apply per candidate
       const int cand = s == 0 ? 1 : s;
@@ -932,9 +932,21 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
       rs = run_common(c, phi, chi, occ, c->d_out_R, nsides == 2 ? c->d_out_L : nullptr, tw, nsides, st, &host_out);
       if (rs != TC_OK) break;
       if (s == 0) continue;
-      const double t_occ = c->stage_ms[2], t_chain = c->stage_ms[3] + c->stage_ms[4];
-      if (t_occ < best_occ) { best_occ = t_occ; so[nsides - 1] = cand; }
-      if (t_chain < best_chain) { best_chain = t_chain; sc[nsides - 1] = cand; }
+      t_occ[s] = c->stage_ms[2];
+      t_chain[s] = c->stage_ms[3] + c->stage_ms[4];
+    }
+    if (rs != TC_OK) break;
+    // the smallest count within 2 % of the fastest: near-ties between counts go the same way
+    // from run to run, and fewer chunks mean fewer partial sums
+    double b_occ = 1e300, b_chain = 1e300;
+    for (int s = 1; s <= smax; ++s) {
+      b_occ = std::min(b_occ, t_occ[s]);
+      b_chain = std::min(b_chain, t_chain[s]);
+    }
+    so[nsides - 1] = sc[nsides - 1] = 0;
+    for (int s = 1; s <= smax; ++s) {
+      if (!so[nsides - 1] && t_occ[s] <= 1.02 * b_occ) so[nsides - 1] = s;
+      if (!sc[nsides - 1] && t_chain[s] <= 1.02 * b_chain) sc[nsides - 1] = s;
     }
   }
   tc_profile(c, prof_was ? 1 : 0);
