@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TC-operator orbital-pair convolutions/sec and % HBM roofline, FP32 vs FP64 at stated error"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # derived ALU peak (FMA = 2 flop)
+HBM_NOMINAL_GBPS = 7900.0
 FFTS_PER_PAIR_CHAIN = 14   # k_pair_chain: rho, 3 pp inverse, 3 pp forward, 3 ap inverse, 3 ap forward, final (with V)
 # DRAM bytes (read + write) of one k_pair_chain<float,24> launch on the 4x4x4 workload, by the partner-chunk
 # count the autotuner chose, each from one 1-pass capture (the autotuner's 18 applies and 3 warm-ups skipped):
@@ -395,7 +396,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2302_07420_gb300 import synth
-    from paper_2302_07420_gb300.operator import Context
+    from paper_2302_07420_gb300.operator import Context, alu_peak
 
     p = (synth.WORKLOADS["si_k444"]() if args.workload == "si_k444"
          else synth.si_params(kmesh=(4, 4, 2) if args.workload == "si_k442" else (2, 2, 2)))
@@ -476,13 +477,22 @@ def main():
     if traffic is not None:
         gbps = traffic / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9
         hbm = {"achieved": gbps, "peak": hbm_peak_gbps(), "unit": "GB/s", "frac": gbps / hbm_peak_gbps(),
-               "what": "ncu DRAM read+write bytes of one launch / its live CUDA-event time (of measured copy peak)"}
+               "nominal_frac": gbps / HBM_NOMINAL_GBPS,
+               "what": "ncu DRAM read+write bytes of one launch / its live CUDA-event time (of measured copy peak; "
+                       "nominal_frac: of the nominal 7.9 TB/s)"}
+    # FFT-pass-equivalent bytes (each n^3 complex64 FFT reads and writes its volume once) per second: a
+    # labelled "effective" rate for comparison with unfused FFT pipelines, not DRAM traffic
+    eff_gbps = chain_pairs * FFTS_PER_PAIR_CHAIN * 2 * N * 8 / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9
+    # measured FMA throughput of the FP32 and FP64 pipes (tc_alu_peak), beside the derived FP32 peak
+    peak32 = alu_peak("fp32", 50.0)
+    peak64 = alu_peak("fp64", 50.0)
 
     # FP64 path (slow on GB300: low FP64 rate), same workload
     ctx64 = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
                     precision="fp64")
     r64, l64 = ctx64.apply(d_phi, d_chi, occ)
     torch.cuda.synchronize()
+    ctx64.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.fp64_steps):
@@ -490,6 +500,9 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / args.fp64_steps
+    pc64_ms, pc64_launch = ctx64.stage_times()["pair_chain"]
+    ctx64.profile(False)
+    achieved64 = flop_per_launch / (pc64_ms / 1e3 / max(pc64_launch, 1)) / 1e12
     ref_scale = max(float(r64.abs().max()), float(l64.abs().max()))
     err32 = max(float((out_r - r64).abs().max()), float((out_l - l64).abs().max())) / ref_scale
     # total energy per cell (Eqs. EtotTC / EtotBiTC): FP32 path against the FP64 path, per electron
@@ -538,13 +551,16 @@ def main():
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_pair_chain",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                          "flop_per_launch": flop_per_launch, "ms_per_launch": pc_ms / max(pc_launch, 1),
-                         "hbm": hbm},
+                         "measured_alu_peak": {"fp32_tflops": peak32, "fp64_tflops": peak64,
+                                               "frac_fp32": achieved / peak32, "source": "tc_alu_peak (FMA chains)"},
+                         "effective_gbs": eff_gbps, "hbm": hbm},
             "e2e": {"value": job_value(world, npairs, args.steps, te), "unit": "pairs/s",
                     "h2d_bytes_per_step": 2 * orb_bytes + occ.nbytes, "d2h_bytes_per_step": 2 * orb_bytes},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "fp64": {"value": npairs / (ms64 / 1e3), "unit": "pairs/s", "ms_per_step": ms64,
-                     "steps": args.fp64_steps},
+                     "steps": args.fp64_steps, "pair_chain_tflops": achieved64,
+                     "pair_chain_frac_of_measured_fp64_peak": achieved64 / peak64},
             "error": {"fp32_vs_fp64_gpu_max_rel": err32, "fp64_gpu_vs_oracle_sampled_max_rel": err_oracle,
                       "energy_fp32_vs_fp64_ha_per_electron": err_e, "energy_fp64_ha_per_cell": e64},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},

@@ -245,6 +245,19 @@ tc_status tc_autotune(tc_ctx* ctx, const void* phi_R, const void* phi_L, const d
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
 tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
 
+/* tc_alu_peak -- measured fused multiply-add throughput of the current
+ * device's non-tensor pipes, the denominator of the roofline of the FFT and
+ * pair-product kernels (the paper has no counterpart: a measurement helper of
+ * this library).  precision TC_FP32 or TC_FP64.  One launch of 16 independent
+ * FMA chains per thread fills every SM; the iteration count doubles from a
+ * short launch until one takes at least target_ms / 2 (0 < target_ms <=
+ * 1000), then the fastest of three launches of that count gives
+ * *tflops = 2 x FMAs / s / 1e12.  Runs on cuda_stream (NULL: legacy default
+ * stream), blocks the host, allocates and frees a small output array.
+ * Errors: TC_ERR_ARG (bad argument), TC_ERR_CUDA (reason in
+ * tc_last_error(NULL)). */
+tc_status tc_alu_peak(int precision, double target_ms, double* tflops, void* cuda_stream);
+
 /* Size of the static device array behind tc_apply_noalloc: 64 MiB per device. */
 #define TC_NOALLOC_MAX_BYTES 67108864
 

@@ -42,7 +42,7 @@ def build(verbose=False, jobs=None, ptxas_info=False):
     steps.append(["g++", "-O2", "-std=c++17", "-fPIC", "-c", os.path.join(SRC, "tc_setup.cpp"),
                   "-o", os.path.join(BUILD, "tc_setup.o")])
     steps.append([nvcc] + NVFLAGS + extra + ["-c", os.path.join(SRC, "tc_api.cu"), "-o", os.path.join(BUILD, "tc_api.o")])
-    for name in ("tc_noalloc", "tc_batch", "tc_davidson", "tc_symmetry"):
+    for name in ("tc_noalloc", "tc_batch", "tc_davidson", "tc_symmetry", "tc_peak"):
         steps.append([nvcc] + NVFLAGS + extra + ["-c", os.path.join(SRC, name + ".cu"),
                                                  "-o", os.path.join(BUILD, name + ".o")])
     for real in REALS:

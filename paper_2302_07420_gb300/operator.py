@@ -244,6 +244,15 @@ def fft3d(x, sign, stream=None):
     return x
 
 
+def alu_peak(precision="fp32", target_ms=50.0, stream=None):
+    """tc_alu_peak: measured FMA throughput (TFLOP/s) of the current device's FP32 or FP64 pipes."""
+    lib = _lib.load()
+    out = ctypes.c_double(0.0)
+    prec = _lib.TC_FP64 if precision in ("fp64", _lib.TC_FP64) else _lib.TC_FP32
+    _lib.check(lib, None, lib.tc_alu_peak(prec, float(target_ms), ctypes.byref(out), _stream_handle(stream)))
+    return out.value
+
+
 class BatchContext:
     """tc_init_batch: many independent cells sharing one workspace, applied by one graph launch.
 

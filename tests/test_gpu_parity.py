@@ -60,6 +60,17 @@ def test_fft3d_matches_numpy(n, prec, sign):
     assert err < (1e-14 if prec == "fp64" else 2e-6), err
 
 
+def test_alu_peak_is_plausible():
+    """tc_alu_peak (the FMA roofline denominator): FP32 at most the derived peak of 152 SMs x 128 lanes x 2
+    flop at 2070 MHz (with 5 % slack) and not far below it; FP64 positive and below FP32."""
+    from paper_2302_07420_gb300.operator import alu_peak
+    derived = 152 * 128 * 2 * 2070e6 / 1e12
+    f32 = alu_peak("fp32", 20.0)
+    f64 = alu_peak("fp64", 20.0)
+    assert 0.3 * derived < f32 < 1.05 * derived, f32
+    assert 0.0 < f64 < f32, (f64, f32)
+
+
 @pytest.mark.parametrize("name", ["heg_14", "si_k444", "heg_114"])
 def test_layout_matches_oracle(name):
     p = synth.WORKLOADS[name]()

@@ -52,3 +52,15 @@ def test_init_error_paths_without_gpu(lib):
     assert lib.tc_init(ctypes.byref(prm), ctypes.byref(h)) == _lib.TC_ERR_ARG
     assert lib.tc_init(None, ctypes.byref(h)) == _lib.TC_ERR_ARG
     assert lib.tc_destroy(None) == _lib.TC_ERR_STATE
+
+
+def test_alu_peak_argument_errors_without_gpu(lib):
+    """tc_alu_peak checks its arguments before any device call."""
+    import ctypes
+    from paper_2302_07420_gb300 import _lib
+    out = ctypes.c_double(0.0)
+    assert lib.tc_alu_peak(7, 50.0, ctypes.byref(out), None) == _lib.TC_ERR_ARG
+    assert lib.tc_alu_peak(_lib.TC_FP32, 0.0, ctypes.byref(out), None) == _lib.TC_ERR_ARG
+    assert lib.tc_alu_peak(_lib.TC_FP64, 5000.0, ctypes.byref(out), None) == _lib.TC_ERR_ARG
+    assert lib.tc_alu_peak(_lib.TC_FP32, 50.0, None, None) == _lib.TC_ERR_ARG
+    assert b"tc_alu_peak" in lib.tc_last_error(None)
