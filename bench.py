@@ -198,8 +198,10 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_sample_pairs_per_s(nsteps=3, kmesh=(2, 2, 1)):
-    """The FP64 CPU oracle on a bounded sample of the workload (same cell and box)."""
+def oracle_sample_pairs_per_s(nsteps=3, kmesh=(2, 2, 1), workers=None):
+    """The FP64 CPU oracle on a bounded sample of the workload (same cell and box); workers = FFT threads
+    (default: all host cores; numpy's pointwise work is single-threaded either way)."""
+    from oracle import backends as B
     from oracle import operator as OP
     from oracle.cell import Setup
     from paper_2302_07420_gb300 import synth
@@ -208,15 +210,49 @@ def oracle_sample_pairs_per_s(nsteps=3, kmesh=(2, 2, 1)):
     c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 1, [S.kpG(k) for k in range(S.Nk)], S.npw_max, S.nbands)
     occ = synth.occupations(S.Nk, S.nbands, S.nocc)
     npairs = pairs_per_apply(S.Nk, S.nbands, S.nocc)
+    saved = B._WORKERS
+    if workers:
+        B._WORKERS = workers
     times = []
-    for _ in range(nsteps):
-        t0 = time.perf_counter()
-        OP.tc_apply(S, c_phi, c_chi, occ)
-        times.append(time.perf_counter() - t0)
-    from oracle.backends import _WORKERS
+    try:
+        for _ in range(nsteps):
+            t0 = time.perf_counter()
+            OP.tc_apply(S, c_phi, c_chi, occ)
+            times.append(time.perf_counter() - t0)
+        used = B._WORKERS
+    finally:
+        B._WORKERS = saved
     return npairs / statistics.median(times), {
-        "cores": _WORKERS, "sample": "si-like cell, 24^3 box, %dx%dx%d k mesh (%d pairs per apply, R+L), "
+        "cores": used, "sample": "si-like cell, 24^3 box, %dx%dx%d k mesh (%d pairs per apply, R+L), "
         "median of %d applies" % (kmesh + (npairs, nsteps)), "seconds": sum(times)}
+
+
+def cufft_comparison(n, ffts_per_launch, chain_ms, dev):
+    """Comparison only (not on the path): the FFTs of one pair-chain launch done as batched cuFFT transforms
+    (torch.fft) that each read and write their n^3 complex64 volume in HBM, without the pointwise passes
+    between them.  A batch of 2048 volumes (226 MB at 24^3, above the 129 MB L2) is timed with CUDA events."""
+    import torch
+    nb = 2048
+    x = torch.randn(nb, n, n, n, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        y = torch.fft.fftn(x, dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        y = torch.fft.fftn(x, dim=(1, 2, 3))
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    per = statistics.median(ts) / nb
+    del x, y
+    torch.cuda.empty_cache()
+    return {"what": "batched cuFFT (torch.fft.fftn) of %d^3 complex64 volumes, out of place, 2048 per call; "
+                    "FFT work of one k_pair_chain launch at that rate, without its pointwise passes" % n,
+            "us_per_volume": 1e3 * per, "hbm_gbs_per_volume_pass": 2 * n ** 3 * 8 / (per / 1e3) / 1e9,
+            "ffts_per_chain_launch": ffts_per_launch, "ffts_only_ms": per * ffts_per_launch,
+            "fused_chain_ms": chain_ms}
 
 
 def measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev):
@@ -234,8 +270,17 @@ def measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev):
     ctx.energy_grad(d_phi, d_chi, occ)
     tg = time.perf_counter() - t0
     nk, nb, no = ctx.nk, p["nbands"], p["nocc"]
-    ctx.close()
     one_side = pairs_per_apply(nk, nb, no) // 2
+    ctx.energy(d_phi, d_chi, occ)
+    te = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        ctx.energy(d_phi, d_chi, occ)
+        te.append(time.perf_counter() - t0)
+    ctx.close()
+    out["energy"] = {"what": "tc_energy: right-side operator + FP64 energy reductions, FP32, same workload "
+                             "(host-synchronous call, wall time, median of 5)",
+                     "ms": 1e3 * statistics.median(te), "pairs_per_s": one_side / statistics.median(te)}
     out["adjoint"] = {"what": "tc_energy_grad: orbital gradients + dE/dA, dE/dC (pp, ap), FP32, same workload",
                       "ms": 1e3 * tg, "passes": "1 two-sided apply + 8 one-sided energies",
                       "pair_convolutions": 2 * one_side + 8 * one_side}
@@ -532,11 +577,15 @@ def main():
     extras = {}
     if not args.no_extras and args.workload == "si_k444":
         extras = measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev)
+        extras["cufft_comparison"] = cufft_comparison(n, chain_pairs * FFTS_PER_PAIR_CHAIN,
+                                                      pc_ms / max(pc_launch, 1), dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, info = oracle_sample_pairs_per_s()
         cpu = {"value": v, "unit": "pairs/s", "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+        v1, info1 = oracle_sample_pairs_per_s(nsteps=1, kmesh=(1, 1, 1), workers=1)
+        cpu["one_thread"] = {"value": v1, "cores": info1["cores"], "sample": info1["sample"]}
 
     if rank == 0:
         line = {
