@@ -60,3 +60,15 @@ def test_kmesh_and_box_conventions():
     assert np.all(f > -0.5) and np.all(f <= 0.5)
     assert CL.fft_rep(6).tolist() == [0, 1, 2, -3, -2, -1]
     assert CL.fft_rep(5).tolist() == [0, 1, 2, -2, -1]
+
+
+def test_heg_cell_from_rs():
+    """HEG geometry (Sec. 4, homogeneous electron gas): four electrons in the simple-cubic cell of
+    a = 7.67663317071 bohr have r_s = 3 bohr, i.e. a = (4 pi N / 3)^(1/3) r_s; the same rule gives the 14- and
+    114-electron cells of the HEG workloads."""
+    p = synth.heg_params(4, 3.0, 16, 4)
+    assert abs(p["lattice"][0, 0] - 7.67663317071) < 1e-10
+    assert np.count_nonzero(p["lattice"] - np.diag(np.diag(p["lattice"]))) == 0
+    Omega = abs(np.linalg.det(p["lattice"]))
+    assert abs((3 * Omega / (4 * np.pi * 4)) ** (1 / 3) - 3.0) < 1e-12
+    assert abs(synth.WORKLOADS["heg_14"]()["lattice"][0, 0] - 15.54052) < 1e-5
