@@ -21,8 +21,11 @@ using the transcorrelated method", arXiv:2302.07420):
                    the TC pseudo-energy (Eqs. EtotTC / EtotBiTC).
 * ``direct``    -- a second backend for ``operator`` that replaces every FFT by
                    direct cyclic sums in reciprocal space (brute force, tiny grids).
-* ``ewald``     -- an Ewald lattice sum of the Madelung potential, used only to pin
-                   the divergence-correction constant.
+* ``band``      -- the operator at band-structure k-points off the SCF mesh
+                   (partners on the mesh), with the band forms of the 2ax and
+                   3b6 corrections (Eqs. divcorr_2ax_band, 3b6_div_band1).
+* ``ewald``     -- Ewald lattice sums (the Madelung potential and its phased
+                   form), used only to pin the divergence-correction constants.
 
 Every floating-point quantity is FP64.  Parity status of each function is stated
 in its module header.
