@@ -33,6 +33,15 @@
  *
  * Errors: no call aborts or throws across the ABI.  On a non-OK status the
  * contents of the output arrays are undefined; tc_last_error gives the reason.
+ * Fault injection (host only, for testing a caller's error handling; the
+ * paper has no counterpart): the environment variable TC_FAULT, read on every
+ * call, makes tc_init and tc_init_batch return TC_ERR_OOM before any device
+ * allocation (TC_FAULT=alloc), and tc_apply, tc_energy, tc_energy_grad,
+ * tc_autotune, tc_davidson_step, tc_apply_batch and tc_apply_noalloc return
+ * TC_ERR_CUDA (TC_FAULT=launch) or TC_ERR_TIMEOUT (TC_FAULT=timeout) before
+ * any kernel launch, with the outputs untouched and the context usable.
+ * TC_ERR_TIMEOUT is otherwise not returned: no kernel of this library waits
+ * on a flag or on another kernel.
  * Threads: a context is not thread-safe; distinct contexts are independent.
  * Streams: work is enqueued on the CUDA stream passed (cudaStream_t, NULL =
  * legacy default stream).  Calls with device pointers return without
@@ -51,7 +60,7 @@ typedef enum {
   TC_ERR_STATE = 2,        /* context not initialised or already destroyed */
   TC_ERR_OOM = 3,          /* device or host allocation failed (tc_init only) */
   TC_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
-  TC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  TC_ERR_TIMEOUT = 5,      /* a bounded device wait gave up (only injected: see TC_FAULT) */
   TC_ERR_UNSUPPORTED = 6,  /* valid but not supported (e.g. FFT box size) */
   TC_ERR_NUMERIC = 7       /* a numerical step failed (vanishing norm, singular overlap,
                               eigen-solver without convergence); outputs undefined */

@@ -1,5 +1,6 @@
 // C ABI of the TC operator library (see include/tc.h).
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -439,6 +440,11 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
     }
     c->left_from_right = clear;
   }
+  if (const int f = injected_fault("alloc")) {
+    err = "injected fault (TC_FAULT=alloc): no device memory allocated";
+    delete c;
+    return f;
+  }
   c->prec = params->precision;
   c->esz = c->prec == TC_FP64 ? 16 : 8;
   c->ws_owned = own_workspace;
@@ -567,6 +573,16 @@ bool device_ptr(const void* p) { return is_device_ptr(p); }
 
 tc_status fail(tc_ctx* c, tc_status s, const std::string& msg) { return ::fail(c, s, msg); }
 
+int injected_fault(const char* site) {
+  const char* v = std::getenv("TC_FAULT");
+  if (!v || !site) return TC_OK;
+  const std::string f(v), at(site);
+  if (at == "alloc" && f == "alloc") return TC_ERR_OOM;
+  if (at == "launch" && f == "launch") return TC_ERR_CUDA;
+  if (at == "launch" && f == "timeout") return TC_ERR_TIMEOUT;
+  return TC_OK;
+}
+
 }  // namespace tc
 
 extern "C" {
@@ -604,6 +620,7 @@ static tc_status run_common(tc_ctx* c, const void* phi, const void* chi, const d
                             const double* tw, int nsides, cudaStream_t st, bool* host_out) {
   const tc::Setup& S = c->S;
   const size_t nj = (size_t)S.Nk * S.nb, orb = nj * S.npw_max * sizeof(double2);
+  if (const int f = tc::injected_fault("launch")) return fail(c, (tc_status)f, "injected fault (TC_FAULT): no device work done");
   const int ro = tc::stage_occ(c, occ, st);
   if (ro != TC_OK) return (tc_status)ro;
   cudaError_t e = cudaSuccess;

@@ -217,6 +217,8 @@ tc_status tc_apply_batch(tc_ctx* c, const void* const* phi_R, const void* const*
   if (!c || !c->batch) return TC_ERR_STATE;
   BatchState* B = c->batch;
   if (!phi_R || !phi_L || !occ || !out_R || !out_L) return tc::fail(c, TC_ERR_ARG, "null pointer array");
+  if (const int f = tc::injected_fault("launch"))
+    return tc::fail(c, (tc_status)f, "injected fault (TC_FAULT): no device work done");
   const int n = (int)B->cells.size();
   std::vector<const void*> key;
   key.reserve(4 * (size_t)n);

@@ -120,6 +120,12 @@ int launch_biortho(tc_ctx* c, double2* phi, double2* chi, int* status, cudaStrea
 constexpr int kBiorthoMaxBands = 64;
 bool device_ptr(const void* p);
 tc_status fail(tc_ctx* c, tc_status s, const std::string& msg);
+// Host-side fault injection for tests of a caller's error handling (no device fault): the
+// environment variable TC_FAULT, read on every call, names the failure.  site "alloc" (context
+// creation, before any device allocation): TC_FAULT=alloc gives TC_ERR_OOM; site "launch" (the
+// operator calls, before any device work): TC_FAULT=launch gives TC_ERR_CUDA, TC_FAULT=timeout
+// TC_ERR_TIMEOUT.  Returns TC_OK when nothing is injected at that site.
+int injected_fault(const char* site);
 void set_thread_error(const std::string& msg);
 
 // Runs the operator pipeline on the given stream.  tw: per-term weights;

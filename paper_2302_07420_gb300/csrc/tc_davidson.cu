@@ -673,6 +673,8 @@ tc_status tc_davidson_step(tc_ctx* c, const void* phi, const void* chi, const do
   const tc::Setup& S = c->S;
   const int m = S.nb, no = S.no, na = no + m;
   if (m > tc::kBiorthoMaxBands) return dav_fail(c, TC_ERR_UNSUPPORTED, "tc_davidson_step supports at most 64 bands");
+  if (const int f = tc::injected_fault("launch"))
+    return dav_fail(c, (tc_status)f, "injected fault (TC_FAULT): no device work done");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tc_status r = ensure_davidson(c);
   if (r != TC_OK) return r;

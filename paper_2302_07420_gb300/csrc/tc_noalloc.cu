@@ -137,6 +137,7 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
                                       const double* occ, void* out_R, void* out_L, void* cuda_stream) {
   if (!params || !phi_R || !phi_L || !occ) return fail(TC_ERR_ARG, "null argument");
   if (!out_R && !out_L) return TC_OK;
+  if (const int f = tc::injected_fault("launch")) return fail((tc_status)f, "injected fault (TC_FAULT): no device work done");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   tc_ctx c;
   const std::string why = tc::build_setup(*params, c.S);

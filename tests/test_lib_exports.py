@@ -64,3 +64,18 @@ def test_alu_peak_argument_errors_without_gpu(lib):
     assert lib.tc_alu_peak(_lib.TC_FP64, 5000.0, ctypes.byref(out), None) == _lib.TC_ERR_ARG
     assert lib.tc_alu_peak(_lib.TC_FP32, 50.0, None, None) == _lib.TC_ERR_ARG
     assert b"tc_alu_peak" in lib.tc_last_error(None)
+
+
+def test_injected_allocation_fault_without_gpu(lib, monkeypatch):
+    """TC_FAULT=alloc: tc_init fails with TC_ERR_OOM after the host setup, before any device call."""
+    import ctypes
+    from paper_2302_07420_gb300 import _lib, synth
+    p = synth.tiny_params(0, kmesh=(1, 1, 2), fft=(9, 9, 9), ecut=1.6, scale=5.0)
+    prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], 3, 2, p["A"], p["C"])
+    h = ctypes.c_void_p()
+    monkeypatch.setenv("TC_FAULT", "alloc")
+    assert lib.tc_init(ctypes.byref(prm), ctypes.byref(h)) == _lib.TC_ERR_OOM
+    assert b"TC_FAULT=alloc" in lib.tc_last_error(None)
+    assert not h.value
+    bad = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], (10, 10, 10), 3, 2, p["A"], p["C"])
+    assert lib.tc_init(ctypes.byref(bad), ctypes.byref(h)) == _lib.TC_ERR_UNSUPPORTED   # setup errors first
