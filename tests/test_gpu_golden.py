@@ -35,14 +35,20 @@ def _ref(g, key, k, nb):
     return np.array(g[key][str(k)]).view(complex).reshape(nb, -1)
 
 
-@pytest.mark.parametrize("prec,tol,etol", [("fp64", 1e-11, 1e-11), ("fp32", 1e-5, 1e-6)])
-def test_full_size_sampled_outputs_and_energy(golden, prec, tol, etol):
+@pytest.mark.parametrize("prec,tol,etol,tuned", [("fp64", 1e-11, 1e-11, False), ("fp32", 1e-5, 1e-6, False),
+                                                  ("fp32", 1e-5, 1e-6, True)])
+def test_full_size_sampled_outputs_and_energy(golden, prec, tol, etol, tuned):
+    """tuned: the launch configuration bench.py times (partner-chunk counts chosen by tc_autotune on these
+    inputs) instead of the default chunk counts."""
     from paper_2302_07420_gb300.operator import Context
     g, p, S, c_phi, c_chi, occ = golden
     ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
                   precision=prec)
     d_phi = torch.from_numpy(c_phi).cuda()
     d_chi = torch.from_numpy(c_chi).cuda()
+    if tuned:
+        so, sc = ctx.autotune(d_phi, d_chi, occ)
+        assert 1 <= so <= 8 and 1 <= sc <= 8
     out_r, out_l = ctx.apply(d_phi, d_chi, occ)
     torch.cuda.synchronize()
     r, l = out_r.cpu().numpy(), out_l.cpu().numpy()
