@@ -25,19 +25,34 @@ the band counterpart of Gamma0 (Eq. correction).  With it:
   3b6  Eq. 3b6_div_band1: the scf1 form with (4 pi A)^2 Gamma0 + x 4 pi A u_short/N_k replaced
        by (4 pi A)^2 Gamma_b.
 
-Not built: the band forms of the grad-u corrections, whose singular parts are
-odd (p/p^2): Eqs. divcorr_2bx1/2, divcorr_3a3, div_corr_3a4_2/3,
-div_corr_3b3_2, div_corr_3b4_2/4, 3b5_div_2/3 and 3b6_div_band2/3.  Off the
-mesh this oracle omits them.  Their common factor, the vector sum
+The grad-u terms have odd singular parts, U(p) ~ i (4 pi A/Omega) p/p^2, and
+Eq. correction_nabla adds -(1/N_k) W(k) . F(0) to a sum (1/N_k) sum (p/p^2) F,
+with the vector sum
 
-  W(k) = sum_{q,G} (k - q + G) A_aux(k - q + G),
+  W(k) = sum_{q,G} (k - q + G) A_aux(k - q + G)
 
-is provided by ``aux_vector_sum``.
+(``aux_vector_sum``; zero on the mesh).  With c = 4 pi A_pp/(N_k Omega),
+O_mj = <bra_m|ket_j> and the band point's own occupied m:
+
+  2bx1  Eq. divcorr_2bx1:  + s i c sum_m f_m O_mj (W . grad ket_m)
+  2bx2  Eq. divcorr_2bx2:  - s i c sum_m f_m (W . <bra_m|grad ket_j>) ket_m
+  3a3   Eq. divcorr_3a3 (on w_j, times h1):  - i c sum_m f_m O_mj (h1 . W) ket_m
+  3b3   Eq. div_corr_3b3_2:  + i c sum_m f_m (W . <bra_m|h1 ket_j>) ket_m
+  3b6   Eqs. 3b6_div_band2/3 (multiplicity 2 times 1/2):
+        - (4 pi A_s/N_k) [O_mj FT^{-1}[(W.G) u~_s n~] + sum_{G != 0} (W.G) u~_s(G) FT[bra_m^* ket_j](G) n~(-G)]
+        times f_m ket_m / Omega^2,
+
+s = +1 right, -1 left (the sign of the grad u . grad terms).  The pairs
+(2bx1, 2bx2), (3a3, 3b3) and (3b6 band2, band3) are each adjoint to each other,
+so <chi_i|h phi_j> = <h^dagger chi_i|phi_j> holds with them and fails if one
+sign of a pair is wrong.  Not built: the band corrections of 3a4, 3b4 and 3b5
+(Eqs. div_corr_3a4_2/3, div_corr_3b4_2/4, 3b5_div_2/3); off the mesh this
+oracle omits them, and w_j enters 3b4 uncorrected.
 
 Pins: tests/test_oracle_band.py (4 pi Gamma_b/Omega against an independent
 phased Ewald sum, alpha-independence of Gamma_b and W, a band point on the
 mesh reproduces the SCF operator, HEG closed forms off the mesh, direct sums,
-adjointness at the band point).
+adjointness at the band point, planted sign errors in each adjoint pair).
 """
 import math
 
@@ -118,6 +133,7 @@ class BandSetup(CL.Setup):
         self.box_index = list(S.box_index) + [tuple((m[:, i] % S.n[i]) for i in range(3)) for m in mb]
         self.gamma_b = [gamma_band(S.lattice, S.kmesh, S.alpha, kcb[i]) if self.on_mesh[i] < 0 else None
                         for i in range(self.nkb)]
+        self.W = [aux_vector_sum(S.lattice, S.kmesh, S.alpha, kcb[i]) for i in range(self.nkb)]
 
 
 class BandOperator(TCOperator):
@@ -163,12 +179,54 @@ class BandOperator(TCOperator):
         one = bk.const(1.0)[None]
         out = bk.zeros((S.nbands,))
         gb = S.gamma_b[k - S.Nk]
+        W = S.W[k - S.Nk]
+        WG = np.einsum("...i,i->...", S.Gbox, W)                              # W . G over the box
+        nt = self.nt
+        ntneg = bk.spec_neg(nt)
+        F = bk.FT(bk.mul(bk.conj(self.bra[k][:no])[:, None], self.ket[k][None]))   # (no, nb)
         for s in range(2):
             c = (FOUR_PI * self.ks.amp(s)) ** 2 * gb
+            a = FOUR_PI * self.ks.amp(s) / S.Nk
+            V2 = bk.iFT(WG * self.us[s] * nt)                                  # band2 field
+            X3 = np.sum(WG * self.us[s] * F * ntneg, axis=(-3, -2, -1))      # band3 scalars (no, nb)
             for q in range(no):
-                field = (c * n0) * O[q][:, None, None, None] * one
+                field = ((c * n0) * O[q][:, None, None, None] * one                   # band1
+                         - a * O[q][:, None, None, None] * V2[None]                   # band2
+                         - a * X3[q][:, None, None, None] * one)                      # band3
                 out = out + self.f[k][q] * bk.mul(self.ket[k][q][None], field) / (Om * Om)
         return out
+
+    def _corr_gradu_band(self, k, acc):
+        """Eqs. divcorr_2bx1/2, divcorr_3a3, div_corr_3b3_2 at an off-mesh band point (added to acc)."""
+        S, bk, no = self.S, self.bk, self.S.nocc
+        W = S.W[k - S.Nk]
+        c = FOUR_PI * self.ks.amp(0) / (S.Nk * S.Omega)
+        f = self.f[k]
+        ket_m, bra_m_c = self.ket[k][:no], bk.conj(self.bra[k][:no])
+        O = self._overlaps(k)                                                  # (no, nb)
+
+        def wsum(vec_field):                                                   # W . (3, grid) -> grid
+            return sum(W[d] * vec_field[..., d, :, :, :] for d in range(3))
+
+        if "2bx1" in acc:
+            Wg = wsum(self.gket[k][:no])                                       # (no, grid): W . grad ket_m
+            acc["2bx1"] = acc["2bx1"] + self.s2b * 1j * c * np.sum(
+                (f[:, None] * O)[:, :, None, None, None] * Wg[:, None], axis=0)
+        if "2bx2" in acc:
+            D = bk.spec_at_zero(bk.FT(bk.mul(bra_m_c[:, None, None], self.gket[k][None])))   # (no, nb, 3)
+            WD = D @ W
+            acc["2bx2"] = acc["2bx2"] - self.s2b * 1j * c * np.sum(
+                (f[:, None] * WD)[:, :, None, None, None] * ket_m[:, None], axis=0)
+        if "3a3" in acc:
+            hW = wsum(self.h1)                                                  # grid
+            t = bk.mul(hW[None], ket_m)                                         # (no, grid)
+            acc["3a3"] = acc["3a3"] - 1j * c * np.sum((f[:, None] * O)[:, :, None, None, None] * t[:, None], axis=0)
+        if "3b3" in acc:
+            hW = wsum(self.h1)
+            E = bk.spec_at_zero(bk.FT(bk.mul(bra_m_c[:, None], bk.mul(hW[None], self.ket[k])[None])))  # (no, nb)
+            acc["3b3"] = acc["3b3"] + 1j * c * np.sum((f[:, None] * E)[:, :, None, None, None] * ket_m[:, None],
+                                                       axis=0)
+        return acc
 
     def apply_band(self, terms=TERMS):
         """Per-term outputs {term: (nkb, nbands, npw_max)} at the band points."""
@@ -178,8 +236,10 @@ class BandOperator(TCOperator):
         for i in range(S.nkb):
             kb = S.Nk + i
             acc = self._apply_k(kb, terms)
-            if "2ax" in acc and S.div_correction and self._off_mesh(kb):
-                acc["2ax"] = acc["2ax"] + self._corr_2ax_band(kb)
+            if S.div_correction and self._off_mesh(kb):
+                if "2ax" in acc:
+                    acc["2ax"] = acc["2ax"] + self._corr_2ax_band(kb)
+                acc = self._corr_gradu_band(kb, acc)
             for t in terms:
                 res[t][i] = self.bk.project(acc[t], kb)
         return res

@@ -7,8 +7,10 @@
   SCF corrections apply on the mesh);
 * HEG plane waves at an off-mesh k: every term is diagonal and equals a finite lattice sum over the
   occupied plane waves of the mesh, derived by hand from the algorithms (Sec. 2.6), plus the band
-  corrections of Eqs. divcorr_2ax_band and 3b6_div_band1;
-* the FFT route equals direct reciprocal-space sums at a band point; adjointness at the band point.
+  corrections of Eqs. divcorr_2ax_band, 3b6_div_band1 and divcorr_2bx1/2;
+* the FFT route equals direct reciprocal-space sums at a band point; adjointness at the band point, which
+  also fails when one member of a pair of grad-u band corrections (2bx1/2bx2, 3a3/3b3, 3b6 band2/band3)
+  has the wrong sign.
 """
 import numpy as np
 import pytest
@@ -127,7 +129,9 @@ def test_adjointness_at_a_band_point(div):
 #   3b6  (nbar/(N_k Omega^2)) sum_P sum_s |D|^2 u~_s(D)^2 + (nbar/Omega^2) sum_s (4 pi A_s)^2 Gamma_b o_n
 #   3a2  the SCF operator's value (h6 is a partner-only, uniform field)
 #   Hartree-type terms vanish (uniform density, G = 0 dropped).
-# The grad-u band corrections are not built, so 2bx1, 2bx2, 3a4, 3b4, 3b5 are the plain sums.
+# Grad-u band corrections (c = 4 pi A_pp/(N_k Omega), W = W(k_b), K_n = k_b + G_n): 2bx1 gains
+# -c (W.K_n) o_n and 2bx2 +c (W.K_n) o_n; those of 3a3, 3b3 and 3b6 (band2/3) vanish (h1 = 0, and n~ has
+# only its G = 0 component); 3a4, 3b4, 3b5 have none built, so they are the plain sums.
 # ---------------------------------------------------------------------------------------------------
 
 def _heg_band_case(kmesh=(2, 2, 1), nbands=9, A=None):
@@ -164,8 +168,9 @@ def _heg_band_closed_forms(S, SB, c, cb, occ_b):
         d2 = np.einsum("ij,ij->i", D, D)
         o = occ_b[0, n] if n < no else 0.0
         e["2ax"][n] = -KN.V2a(d2, A[0], C[0]).sum() / (Nk * Om) - 4 * np.pi * gb / Om * o
-        e["2bx1"][n] = np.einsum("ij,ij->i", P, D) @ u(0, D) / (Nk * Om)
-        e["2bx2"][n] = -(D @ Kn[n]) @ u(0, D) / (Nk * Om)
+        cW = 4 * np.pi * A[0] / (Nk * Om) * (SB.W[0] @ Kn[n]) * o
+        e["2bx1"][n] = np.einsum("ij,ij->i", P, D) @ u(0, D) / (Nk * Om) - cW
+        e["2bx2"][n] = -(D @ Kn[n]) @ u(0, D) / (Nk * Om) + cW
         ab = U(D).sum(axis=0) / Nk
         e["3b4"][n] = ab @ ab
         e["3a4"][n] = -np.einsum("ij,ij->", a, U(D)) / Nk
@@ -203,3 +208,47 @@ def test_band_pins_detect_a_planted_mistake(monkeypatch):
     idx = [int(np.argmax(np.abs(cb[0, b]))) for b in range(cb.shape[1])]
     ev = np.array([res["2ax"][0, b, idx[b]] for b in range(len(idx))])
     assert np.abs(ev - ref["2ax"]).max() > 1e-4 * np.abs(ref["2ax"]).max()
+
+
+@pytest.mark.parametrize("pair", ["2bx", "3a3b3", "3b6"])
+def test_adjointness_catches_a_sign_error_in_each_corrected_pair(pair, monkeypatch):
+    """Each pair of grad-u band corrections is adjoint to itself as a pair: flipping one member breaks
+    <chi_i|h phi_j> = <h^dagger chi_i|phi_j> at the band point."""
+    S, c_phi, c_chi, occ = _tiny(2)
+    SB, b_phi, b_chi, b_occ = _band_orbitals(S, K_OFF, 2)
+    if pair == "3b6":
+        orig = BD.BandOperator._corr_3b6
+
+        def band3(self, k):
+            # the band3 part of the 3b6 correction alone (Eq. 3b6_div_band3, oracle normalisation)
+            S_, bk = self.S, self.bk
+            no, Om = S_.nocc, S_.Omega
+            WG = np.einsum("...i,i->...", S_.Gbox, S_.W[k - S_.Nk])
+            F = bk.FT(bk.mul(bk.conj(self.bra[k][:no])[:, None], self.ket[k][None]))
+            out = bk.zeros((S_.nbands,))
+            for s_ in range(2):
+                a = 4 * np.pi * self.ks.amp(s_) / S_.Nk
+                X3 = np.sum(WG * self.us[s_] * F * bk.spec_neg(self.nt), axis=(-3, -2, -1))
+                for q in range(no):
+                    field = -a * X3[q][:, None, None, None] * bk.const(1.0)[None]
+                    out = out + self.f[k][q] * bk.mul(self.ket[k][q][None], field) / (Om * Om)
+            return out
+
+        def flipped(self, k):
+            return orig(self, k) - 2.0 * band3(self, k)      # band3 with the wrong sign
+        monkeypatch.setattr(BD.BandOperator, "_corr_3b6", flipped)
+    else:
+        orig = BD.BandOperator._corr_gradu_band
+        term = "2bx2" if pair == "2bx" else "3b3"
+
+        def flipped(self, k, acc):
+            before = acc[term].copy()
+            acc = orig(self, k, acc)
+            acc[term] = 2 * before - acc[term]      # this member's correction with the wrong sign
+            return acc
+        monkeypatch.setattr(BD.BandOperator, "_corr_gradu_band", flipped)
+    r = OP.total(BD.band_apply(S, c_phi, c_chi, occ, K_OFF, b_phi, b_chi, b_occ))
+    l = OP.total(BD.band_apply(S, c_phi, c_chi, occ, K_OFF, b_phi, b_chi, b_occ, left=True))
+    lhs = np.conj(b_chi[0]) @ r[0].T
+    rhs = np.conj(l[0]) @ b_phi[0].T
+    assert np.abs(lhs - rhs).max() > 1e-9 * np.abs(lhs).max()
