@@ -42,12 +42,18 @@ O_mj = <bra_m|ket_j> and the band point's own occupied m:
         - (4 pi A_s/N_k) [O_mj FT^{-1}[(W.G) u~_s n~] + sum_{G != 0} (W.G) u~_s(G) FT[bra_m^* ket_j](G) n~(-G)]
         times f_m ket_m / Omega^2,
 
-s = +1 right, -1 left (the sign of the grad u . grad terms).  The pairs
-(2bx1, 2bx2), (3a3, 3b3) and (3b6 band2, band3) are each adjoint to each other,
-so <chi_i|h phi_j> = <h^dagger chi_i|phi_j> holds with them and fails if one
-sign of a pair is wrong.  Not built: the band corrections of 3a4, 3b4 and 3b5
-(Eqs. div_corr_3a4_2/3, div_corr_3b4_2/4, 3b5_div_2/3); off the mesh this
-oracle omits them, and w_j enters 3b4 uncorrected.
+  3a4   Eqs. div_corr_3a4_2/3:  + i c sum_m f_m O_mj (W . h3a(m))
+  3b5   Eqs. 3b5_div_2/3:  - i c sum_m f_m (W . FT[ket_j h3b(m)](0)) ket_m
+  3b4   Eq. div_corr_3b4_2 (w_j -> w_j + w_c, w_c = -i c W sum_m f_m O_mj ket_m, the
+        3a3 correction) and Eq. div_corr_3b4_4: - i c sum_m f_m (W . <bra_m|w_j + w_c>) ket_m,
+
+s = +1 right, -1 left (the sign of the grad u . grad terms), where h3a(m),
+h3b(m) are the occupied-pair fields of the band point's own occupied orbitals
+(``_band_h3``), themselves corrected for q1 -> k_b, which gives the W . W terms
+of Eqs. div_corr_3a4_3 and 3b5_div_3.  The pairs (2bx1, 2bx2), (3a3, 3b3),
+(3a4, 3b5) and (3b6 band2, band3) are each adjoint to each other and the 3b4
+corrections to themselves, so <chi_i|h phi_j> = <h^dagger chi_i|phi_j> holds
+with them and fails if one sign of a pair is wrong.
 
 Pins: tests/test_oracle_band.py (4 pi Gamma_b/Omega against an independent
 phased Ewald sum, alpha-independence of Gamma_b and W, a band point on the
@@ -226,7 +232,53 @@ class BandOperator(TCOperator):
             E = bk.spec_at_zero(bk.FT(bk.mul(bra_m_c[:, None], bk.mul(hW[None], self.ket[k])[None])))  # (no, nb)
             acc["3b3"] = acc["3b3"] + 1j * c * np.sum((f[:, None] * E)[:, :, None, None, None] * ket_m[:, None],
                                                        axis=0)
+        if "3a4" in acc or "3b5" in acc:
+            h3a, h3b = self._band_h3(k)
+            if "3a4" in acc:     # Eqs. div_corr_3a4_2/3: + i c sum_m f_m O_mj (W . h3a(m))
+                t = wsum(h3a)                                                   # (no, grid)
+                acc["3a4"] = acc["3a4"] + 1j * c * np.sum((f[:, None] * O)[:, :, None, None, None] * t[:, None],
+                                                           axis=0)
+            if "3b5" in acc:     # Eqs. 3b5_div_2/3: - i c sum_m f_m (W . FT[ket_j h3b(m)](0)) ket_m
+                E = bk.spec_at_zero(bk.FT(bk.mul(self.ket[k][None, :, None], h3b[:, None])))   # (no, nb, 3)
+                acc["3b5"] = acc["3b5"] - 1j * c * np.sum((f[:, None] * (E @ W))[:, :, None, None, None]
+                                                          * ket_m[:, None], axis=0)
+        if "3b4" in acc:         # Eqs. div_corr_3b4_2 (on w_j) and div_corr_3b4_4
+            wc = -1j * c * np.einsum("d,mj,m...->jd...", W, f[:, None] * O, ket_m)      # correction of w_j
+            w = self._w_last + wc
+            acc["3b4"] = acc["3b4"] - self._pass_3b4(k, wc)
+            E = bk.spec_at_zero(bk.FT(bk.mul(bra_m_c[:, None, None], w[None])))          # (no, nb, 3)
+            acc["3b4"] = acc["3b4"] - 1j * c * np.sum((f[:, None] * (E @ W))[:, :, None, None, None]
+                                                      * ket_m[:, None], axis=0)
         return acc
+
+    def _band_h3(self, k):
+        """h3 of both kinds for the band point's own occupied orbitals m (q2 at k_b, partners q1 on the
+        mesh; Algs. 6 and 8 with kernels at k_b - q1 + G and q1 - k_b + G), each with the correction of
+        Eq. correction_nabla for q1 -> k_b (the source of Eqs. div_corr_3a4_3 and 3b5_div_3):
+          h3a(m) = sum_q1 f/N_k P(q1, m) ket_q1   - i c W sum_m' f_m' <bra_m'|ket_m> ket_m'
+          h3b(m) = sum_q1 f/N_k P(m, q1) bra_q1^* + i c W sum_m' f_m' <bra_m|ket_m'> bra_m'^*
+        Returns (h3a, h3b), each (nocc, 3, grid)."""
+        S, bk = self.S, self.bk
+        Nk, no = S.Nk, S.nocc
+        c = FOUR_PI * self.ks.amp(0) / (Nk * S.Omega)
+        W = S.W[k - Nk]
+        ket_m, bra_m_c = self.ket[k][:no], bk.conj(self.bra[k][:no])
+        h3a = bk.zeros((no, 3))
+        h3b = bk.zeros((no, 3))
+        for k1 in range(Nk):
+            f1 = self.f[k1] / Nk
+            bra1_c, ket1 = bk.conj(self.bra[k1][:no]), self.ket[k1][:no]
+            KB = self.kern(k, k1)                                                   # p = k_b - q1 + G
+            PB = bk.iFT(KB["U"][0][None, None] * bk.FT(bk.mul(bra1_c[:, None], ket_m[None]))[:, :, None])
+            h3a = h3a + np.sum(f1[:, None, None, None, None, None] * bk.mul(PB, ket1[:, None, None]), axis=0)
+            KA = self.kern(k1, k)                                                   # p = q1 - k_b + G
+            PA = bk.iFT(KA["U"][0][None, None] * bk.FT(bk.mul(bra_m_c[:, None], ket1[None]))[:, :, None])
+            h3b = h3b + np.sum(f1[None, :, None, None, None, None] * bk.mul(PA, bra1_c[None, :, None]), axis=1)
+        Ob = self._overlaps(k)[:, :no]                                             # [m', m] = <bra_m'|ket_m>
+        f = self.f[k]
+        h3a = h3a - 1j * c * np.einsum("d,pm,p...->md...", W, f[:, None] * Ob, ket_m)
+        h3b = h3b + 1j * c * np.einsum("d,mp,p...->md...", W, Ob * f[None, :], bra_m_c)
+        return h3a, h3b
 
     def apply_band(self, terms=TERMS):
         """Per-term outputs {term: (nkb, nbands, npw_max)} at the band points."""

@@ -310,13 +310,9 @@ class TCOperator:
                     X = bk.FT(bk.mul(self.n[None, None, None], h2U[s]))
                     Ysum = Ysum + np.sum(-K["U"][s][None, None] * X, axis=2)
                 acc["3b6"] += fsum(fq, bk.mul(ketq[:, None], bk.iFT(Ysum)))
+        self._w_last = w       # w_j of this k-point (read by the band-point corrections)
         if "3b4" in acc:       # second pass: w_j is complete; 2 * (-1/2)
-            for kq in range(Nk):
-                K = self.kern(k, kq)
-                braq_c = bk.conj(self.bra[kq][:no])
-                X = bk.FT(bk.mul(braq_c[:, None, None], w[None]))
-                Y = bk.iFT(np.sum(-K["U"][0][None, None] * X, axis=2))
-                acc["3b4"] -= fsum(self.f[kq] / Nk, bk.mul(self.ket[kq][:no][:, None], Y))
+            acc["3b4"] -= self._pass_3b4(k, w)
         # Hartree-type (local) terms
         if "2ah" in acc:
             acc["2ah"] += bk.mul(self.vH[None], ketj)
@@ -337,6 +333,20 @@ class TCOperator:
         if "3b6" in acc and S.div_correction:
             acc["3b6"] += self._corr_3b6(k)
         return acc
+
+    def _pass_3b4(self, k, w):
+        """Alg. 10 for the orbitals of k-point k given w (nb, 3, grid): sum_q f/N_k ket_q FT^{-1}[-U . FT[bra_q^* w]]."""
+        S, bk = self.S, self.bk
+        Nk, no = S.Nk, S.nocc
+        out = 0.0
+        for kq in range(Nk):
+            K = self.kern(k, kq)
+            braq_c = bk.conj(self.bra[kq][:no])
+            X = bk.FT(bk.mul(braq_c[:, None, None], w[None]))
+            Y = bk.iFT(np.sum(-K["U"][0][None, None] * X, axis=2))
+            fq = self.f[kq] / Nk
+            out = out + np.sum(fq.reshape((-1,) + (1,) * (Y.ndim - 1)) * bk.mul(self.ket[kq][:no][:, None], Y), axis=0)
+        return out
 
     def _corr_3b6(self, k):
         """Eqs. 3b6_div_scf1/2/3 (times the multiplicity 2 of 3b*, times 1/2 of 3b6)."""

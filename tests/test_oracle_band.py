@@ -7,10 +7,11 @@
   SCF corrections apply on the mesh);
 * HEG plane waves at an off-mesh k: every term is diagonal and equals a finite lattice sum over the
   occupied plane waves of the mesh, derived by hand from the algorithms (Sec. 2.6), plus the band
-  corrections of Eqs. divcorr_2ax_band, 3b6_div_band1 and divcorr_2bx1/2;
+  corrections (Eqs. divcorr_2ax_band, 3b6_div_band1, divcorr_2bx1/2, div_corr_3a4_2/3, 3b5_div_2/3,
+  div_corr_3b4_2/4);
 * the FFT route equals direct reciprocal-space sums at a band point; adjointness at the band point, which
-  also fails when one member of a pair of grad-u band corrections (2bx1/2bx2, 3a3/3b3, 3b6 band2/band3)
-  has the wrong sign.
+  also fails when one member of a pair of grad-u band corrections (2bx1/2bx2, 3a3/3b3, 3a4/3b5,
+  3b6 band2/band3) or a 3b4 correction has the wrong sign.
 """
 import numpy as np
 import pytest
@@ -130,8 +131,10 @@ def test_adjointness_at_a_band_point(div):
 #   3a2  the SCF operator's value (h6 is a partner-only, uniform field)
 #   Hartree-type terms vanish (uniform density, G = 0 dropped).
 # Grad-u band corrections (c = 4 pi A_pp/(N_k Omega), W = W(k_b), K_n = k_b + G_n): 2bx1 gains
-# -c (W.K_n) o_n and 2bx2 +c (W.K_n) o_n; those of 3a3, 3b3 and 3b6 (band2/3) vanish (h1 = 0, and n~ has
-# only its G = 0 component); 3a4, 3b4, 3b5 have none built, so they are the plain sums.
+# -c (W.K_n) o_n and 2bx2 +c (W.K_n) o_n; 3a4 and 3b5 gain i c o_n (W.a_b(n)) + c^2 o_n^2 (W.W) (the band
+# point's own h3 fields are (a_b(n) - i c W o_n) e^{iG_n.r} and (-a_b(n) + i c W o_n) e^{-iG_n.r});
+# 3b4 becomes a_b.a_b - 2 i c o_n (W.a_b) - c^2 o_n^2 (W.W); those of 3a3, 3b3 and 3b6 (band2/3) vanish
+# (h1 = 0, and n~ has only its G = 0 component).
 # ---------------------------------------------------------------------------------------------------
 
 def _heg_band_case(kmesh=(2, 2, 1), nbands=9, A=None):
@@ -172,8 +175,10 @@ def _heg_band_closed_forms(S, SB, c, cb, occ_b):
         e["2bx1"][n] = np.einsum("ij,ij->i", P, D) @ u(0, D) / (Nk * Om) - cW
         e["2bx2"][n] = -(D @ Kn[n]) @ u(0, D) / (Nk * Om) + cW
         ab = U(D).sum(axis=0) / Nk
-        e["3b4"][n] = ab @ ab
-        e["3a4"][n] = -np.einsum("ij,ij->", a, U(D)) / Nk
+        c = 4 * np.pi * A[0] / (Nk * Om)
+        W = SB.W[0]
+        e["3b4"][n] = ab @ ab - 2j * c * o * (W @ ab) - (c * o) ** 2 * (W @ W)
+        e["3a4"][n] = -np.einsum("ij,ij->", a, U(D)) / Nk + 1j * c * o * (W @ ab) + (c * o) ** 2 * (W @ W)
         e["3b5"][n] = e["3a4"][n]
         e["3b6"][n] = (no / (Nk * Om ** 2)) * sum(d2 @ u(s, D) ** 2 for s in range(2)) \
             + (no / Om ** 2) * sum((4 * np.pi * A[s]) ** 2 for s in range(2)) * gb * o
@@ -210,7 +215,7 @@ def test_band_pins_detect_a_planted_mistake(monkeypatch):
     assert np.abs(ev - ref["2ax"]).max() > 1e-4 * np.abs(ref["2ax"]).max()
 
 
-@pytest.mark.parametrize("pair", ["2bx", "3a3b3", "3b6"])
+@pytest.mark.parametrize("pair", ["2bx", "3a3b3", "3a4b5", "3b4", "3b6"])
 def test_adjointness_catches_a_sign_error_in_each_corrected_pair(pair, monkeypatch):
     """Each pair of grad-u band corrections is adjoint to itself as a pair: flipping one member breaks
     <chi_i|h phi_j> = <h^dagger chi_i|phi_j> at the band point."""
@@ -239,9 +244,19 @@ def test_adjointness_catches_a_sign_error_in_each_corrected_pair(pair, monkeypat
         monkeypatch.setattr(BD.BandOperator, "_corr_3b6", flipped)
     else:
         orig = BD.BandOperator._corr_gradu_band
-        term = "2bx2" if pair == "2bx" else "3b3"
 
         def flipped(self, k, acc):
+            if pair == "3b4":
+                # the 3b4 correction is adjoint to itself as a whole; its w_j part (Eq. div_corr_3b4_2) and
+                # Eq. div_corr_3b4_4 are each other's adjoint: flip the sign of the w_j part only
+                acc = orig(self, k, acc)
+                S_, no = self.S, self.S.nocc
+                c = 4 * np.pi * self.ks.amp(0) / (S_.Nk * S_.Omega)
+                wc = -1j * c * np.einsum("d,mj,m...->jd...", S_.W[k - S_.Nk], self.f[k][:, None] * self._overlaps(k),
+                                         self.ket[k][:no])
+                acc["3b4"] = acc["3b4"] + 2.0 * self._pass_3b4(k, wc)
+                return acc
+            term = {"2bx": "2bx2", "3a3b3": "3b3", "3a4b5": "3b5"}[pair]
             before = acc[term].copy()
             acc = orig(self, k, acc)
             acc[term] = 2 * before - acc[term]      # this member's correction with the wrong sign
