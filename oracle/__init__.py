@@ -22,8 +22,9 @@ using the transcorrelated method", arXiv:2302.07420):
 * ``direct``    -- a second backend for ``operator`` that replaces every FFT by
                    direct cyclic sums in reciprocal space (brute force, tiny grids).
 * ``band``      -- the operator at band-structure k-points off the SCF mesh
-                   (partners on the mesh), with the band forms of the 2ax and
-                   3b6 corrections (Eqs. divcorr_2ax_band, 3b6_div_band1).
+                   (partners on the mesh) with the band forms of every
+                   divergence correction (Eq. divcorr_2ax_band, the grad-u
+                   forms of Eq. correction_nabla, Eqs. 3b6_div_band1/2/3).
 * ``ewald``     -- Ewald lattice sums (the Madelung potential and its phased
                    form), used only to pin the divergence-correction constants.
 
