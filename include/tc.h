@@ -254,6 +254,23 @@ tc_status tc_autotune(tc_ctx* ctx, const void* phi_R, const void* phi_L, const d
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
 tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
 
+/* tc_band_constants -- the constants of the divergence corrections at
+ * band-structure k-points off the SCF mesh (Sec. 2.6.3 after Eq.
+ * divcorr_2ax_scf: Eqs. divcorr_2ax_band and 3b6_div_band1 use the scalar,
+ * the grad-u band forms of Eq. correction_nabla the vector), with q over the
+ * SCF mesh and alpha of params (0: the default):
+ *   gamma_b[i]    = Omega/(4 sqrt(pi^3 alpha)) - (1/N_k) sum_{q,G} A_aux(k_i - q + G)
+ *   W[3i .. 3i+2] = sum_{q,G} (k_i - q + G) A_aux(k_i - q + G)      (Cartesian, bohr)
+ * A_aux(p) = exp(-alpha p^2)/p^2; 4 pi gamma_b/Omega equals minus the
+ * Ewald-summed sum_{R != 0} cos(k.R)/|R| over the Born-von Karman supercell.
+ * kfrac_band: [nkb][3] fractional coordinates in the reciprocal basis (host).
+ * Host only, FP64, no device work (needs no GPU).  Errors: TC_ERR_ARG (null
+ * pointer, nkb < 0, invalid params, a point on the SCF mesh modulo a
+ * reciprocal vector: such a point takes the SCF constant Gamma0),
+ * TC_ERR_UNSUPPORTED (box size); reason in tc_last_error(NULL). */
+tc_status tc_band_constants(const tc_params* params, const double* kfrac_band, int nkb, double* gamma_b,
+                            double* W);
+
 /* tc_alu_peak -- measured fused multiply-add throughput of the current
  * device's non-tensor pipes, the denominator of the roofline of the FFT and
  * pair-product kernels (the paper has no counterpart: a measurement helper of

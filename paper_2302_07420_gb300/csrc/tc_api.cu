@@ -901,6 +901,42 @@ tc_status tc_fft3d(int n, int precision, int sign, void* data, int batch, void* 
   return (tc_status)r;
 }
 
+tc_status tc_band_constants(const tc_params* params, const double* kfrac_band, int nkb, double* gamma_b,
+                            double* W) {
+  if (!params || nkb < 0 || (nkb > 0 && (!kfrac_band || !gamma_b || !W))) {
+    tc::set_thread_error("tc_band_constants: null pointer or nkb < 0");
+    return TC_ERR_ARG;
+  }
+  tc::Setup S;
+  const std::string why = tc::build_setup(*params, S);
+  if (!why.empty()) {
+    tc::set_thread_error("tc_band_constants: " + why);
+    return why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
+  }
+  for (int i = 0; i < nkb; ++i) {
+    const double* kf = kfrac_band + 3 * (size_t)i;
+    for (int q = 0; q < S.Nk; ++q) {
+      bool same = true;
+      for (int d = 0; d < 3; ++d) {
+        const double x = kf[d] - S.kfrac[q][d];
+        same = same && std::fabs(x - std::round(x)) < 1e-12;
+      }
+      if (same) {
+        tc::set_thread_error("tc_band_constants: band point " + std::to_string(i) +
+                         " lies on the SCF mesh (it takes the SCF constants)");
+        return TC_ERR_ARG;
+      }
+    }
+    double k[3];
+    for (int d = 0; d < 3; ++d) k[d] = kf[0] * S.B[0][d] + kf[1] * S.B[1][d] + kf[2] * S.B[2][d];
+    if (!tc::band_constants(S, k, gamma_b + i, W + 3 * (size_t)i)) {
+      tc::set_thread_error("tc_band_constants: band point " + std::to_string(i) + " lies on the SCF mesh");
+      return TC_ERR_ARG;
+    }
+  }
+  return TC_OK;
+}
+
 tc_status tc_profile(tc_ctx* c, int enable) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");

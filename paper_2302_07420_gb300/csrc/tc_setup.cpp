@@ -190,6 +190,51 @@ static double aux_sum(const Setup& S, double alpha) {
   return s;
 }
 
+// Neumaier's compensated sum (terms of both signs).
+namespace {
+struct CompSum {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    const double t = s + x;
+    c += std::fabs(s) >= std::fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
+}  // namespace
+
+bool band_constants(const Setup& S, const double kcart[3], double* gamma_b, double W[3]) {
+  const double alpha = S.alpha;
+  const double kn = norm3(kcart);
+  const double pmax = std::sqrt(-std::log(1e-20) / alpha) + kn;
+  int bound[3];
+  double Bs[3][3];
+  for (int i = 0; i < 3; ++i) {
+    const double L = norm3(S.A[i]) * S.prm.kmesh[i];
+    bound[i] = (int)std::ceil(pmax * L / (2.0 * kPi)) + 1;
+    for (int d = 0; d < 3; ++d) Bs[i][d] = S.B[i][d] / S.prm.kmesh[i];
+  }
+  std::vector<double> w;
+  CompSum wv[3];
+  for (int a = -bound[0]; a <= bound[0]; ++a)
+    for (int b = -bound[1]; b <= bound[1]; ++b)
+      for (int c = -bound[2]; c <= bound[2]; ++c) {
+        double p[3];
+        for (int d = 0; d < 3; ++d) p[d] = kcart[d] - (a * Bs[0][d] + b * Bs[1][d] + c * Bs[2][d]);
+        const double p2 = p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+        if (p2 == 0.0) return false;
+        const double t = std::exp(-alpha * p2) / p2;
+        w.push_back(t);
+        for (int d = 0; d < 3; ++d) wv[d].add(p[d] * t);
+      }
+  std::sort(w.begin(), w.end());
+  double s = 0.0;
+  for (double x : w) s += x;
+  *gamma_b = S.Omega / (4.0 * std::sqrt(kPi * kPi * kPi * alpha)) - s / S.Nk;
+  for (int d = 0; d < 3; ++d) W[d] = wv[d].value();
+  return true;
+}
+
 static int fft_rep(int m, int n) { return m <= (n - 1) / 2 ? m : m - n; }
 
 std::string build_setup(const tc_params& p, Setup& S) {

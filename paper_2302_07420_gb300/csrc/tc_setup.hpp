@@ -50,6 +50,13 @@ void kernel_data(const Setup& S, int mode, KernelData& kd);
 // Returns an empty string on success, otherwise the reason.
 std::string build_setup(const tc_params& p, Setup& S);
 
+// Constants of the divergence corrections at a band-structure k-point off the SCF mesh
+// (Sec. 2.6.3 after Eq. divcorr_2ax_scf; Eqs. divcorr_2ax_band, correction_nabla), for
+// kcart = k: gamma_b = Omega/(4 sqrt(pi^3 alpha)) - (1/Nk) sum_{q,G} A_aux(k - q + G) and
+// W = sum_{q,G} (k - q + G) A_aux(k - q + G), A_aux(p) = exp(-alpha p^2)/p^2, q over the SCF mesh.
+// Returns false when some k - q + G vanishes (k on the mesh).
+bool band_constants(const Setup& S, const double kcart[3], double* gamma_b, double W[3]);
+
 // Appendix B kernel pieces (host, FP64), exposed for the table tests.
 double host_u_tilde(double p2, double A, double C);
 double host_gradu_sq(double p, double A, double C);

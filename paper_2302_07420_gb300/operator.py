@@ -253,6 +253,21 @@ def alu_peak(precision="fp32", target_ms=50.0, stream=None):
     return out.value
 
 
+def band_constants(lattice, kmesh, ecut, fft, nbands, nocc, A, C, kfrac_band, alpha=0.0):
+    """tc_band_constants: (gamma_b (nkb,), W (nkb, 3)) of band points kfrac_band off the SCF mesh (host only)."""
+    lib = _lib.load()
+    prm = _lib.make_params(lattice, kmesh, ecut, fft, nbands, nocc, A, C, alpha)
+    kf = np.ascontiguousarray(np.atleast_2d(kfrac_band), dtype=np.float64)
+    n = kf.shape[0]
+    g = np.zeros(n)
+    W = np.zeros((n, 3))
+    dp = ctypes.POINTER(ctypes.c_double)
+    st = lib.tc_band_constants(ctypes.byref(prm), kf.ctypes.data_as(dp), n, g.ctypes.data_as(dp),
+                               W.ctypes.data_as(dp))
+    _lib.check(lib, None, st)
+    return g, W
+
+
 class BatchContext:
     """tc_init_batch: many independent cells sharing one workspace, applied by one graph launch.
 
