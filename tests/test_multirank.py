@@ -59,3 +59,24 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_value_is_pairs_over_seconds(monkeypatch, capsys):
+    """The reference line's value is the pairs of all timed steps over their total seconds."""
+    import argparse
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    secs = iter([9.0, 2.0, 3.0])                 # one warm-up, two timed steps
+
+    def fake(nsteps=3, kmesh=(2, 1, 1), workers=None):
+        s = next(secs)
+        return 256 / s, {"cores": 4, "sample": "fake", "seconds": s}
+    monkeypatch.setattr(bench, "oracle_sample_pairs_per_s", fake)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.run_reference(argparse.Namespace(warmup=1, steps=2, gpus=1))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert abs(line["value"] - 2 * 256 / 5.0) < 1e-9
+    assert abs(line["ms_per_step"] - 2500.0) < 1e-9
+    assert line["cpu_baseline"]["value"] == line["value"] and line["e2e"]["value"] == line["value"]
