@@ -270,6 +270,17 @@ tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
  * TC_ERR_UNSUPPORTED (box size); reason in tc_last_error(NULL). */
 tc_status tc_band_constants(const tc_params* params, const double* kfrac_band, int nkb, double* gamma_b,
                             double* W);
+/* tc_band_layout -- the plane-wave spheres of band-structure k-points (the
+ * layout of orbitals at band points off the SCF mesh): for band point i,
+ * npw[i] <- the number of Miller vectors m with |k_i + m.B|^2/2 <= ecut_ha,
+ * and, if miller is not NULL, miller[i][g][3] <- those vectors in
+ * lexicographic order (the order of every sphere of tc_layout), zero padded
+ * to max_npw per point.  kfrac_band: [nkb][3] fractional coordinates (host);
+ * call once with miller = NULL for the counts.  Host only, no device work.
+ * Errors: TC_ERR_ARG (null pointer, nkb < 0, max_npw too small, a sphere that
+ * does not fit the FFT box, invalid params), TC_ERR_UNSUPPORTED (box size). */
+tc_status tc_band_layout(const tc_params* params, const double* kfrac_band, int nkb, int max_npw, int* npw,
+                         int* miller);
 
 /* tc_alu_peak -- measured fused multiply-add throughput of the current
  * device's non-tensor pipes, the denominator of the roofline of the FFT and

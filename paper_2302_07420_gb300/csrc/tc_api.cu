@@ -1,5 +1,6 @@
 // C ABI of the TC operator library (see include/tc.h).
 #include <algorithm>
+#include <array>
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
@@ -933,6 +934,41 @@ tc_status tc_band_constants(const tc_params* params, const double* kfrac_band, i
       tc::set_thread_error("tc_band_constants: band point " + std::to_string(i) + " lies on the SCF mesh");
       return TC_ERR_ARG;
     }
+  }
+  return TC_OK;
+}
+
+tc_status tc_band_layout(const tc_params* params, const double* kfrac_band, int nkb, int max_npw, int* npw,
+                         int* miller) {
+  if (!params || nkb < 0 || (nkb > 0 && (!kfrac_band || !npw)) || (miller && max_npw <= 0)) {
+    tc::set_thread_error("tc_band_layout: null pointer, nkb < 0 or max_npw <= 0");
+    return TC_ERR_ARG;
+  }
+  tc::Setup S;
+  const std::string why = tc::build_setup(*params, S);
+  if (!why.empty()) {
+    tc::set_thread_error("tc_band_layout: " + why);
+    return why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
+  }
+  std::vector<std::array<int, 3>> m;
+  for (int i = 0; i < nkb; ++i) {
+    const double* kf = kfrac_band + 3 * (size_t)i;
+    double k[3];
+    for (int d = 0; d < 3; ++d) k[d] = kf[0] * S.B[0][d] + kf[1] * S.B[1][d] + kf[2] * S.B[2][d];
+    if (!tc::sphere(S, k, m)) {
+      tc::set_thread_error("tc_band_layout: the sphere of band point " + std::to_string(i) +
+                           " does not fit the FFT box");
+      return TC_ERR_ARG;
+    }
+    npw[i] = (int)m.size();
+    if (!miller) continue;
+    if (npw[i] > max_npw) {
+      tc::set_thread_error("tc_band_layout: max_npw is smaller than the sphere of band point " + std::to_string(i));
+      return TC_ERR_ARG;
+    }
+    int* out = miller + (size_t)i * max_npw * 3;
+    for (int g = 0; g < max_npw; ++g)
+      for (int d = 0; d < 3; ++d) out[3 * g + d] = g < npw[i] ? m[g][d] : 0;
   }
   return TC_OK;
 }

@@ -235,6 +235,26 @@ bool band_constants(const Setup& S, const double kcart[3], double* gamma_b, doub
   return true;
 }
 
+bool sphere(const Setup& S, const double kcart[3], std::vector<std::array<int, 3>>& out) {
+  out.clear();
+  const int n = S.prm.fft[0];
+  const double ecut = S.prm.ecut_ha;
+  const double gmax = std::sqrt(2.0 * ecut) + norm3(kcart);
+  int bound[3];
+  for (int i = 0; i < 3; ++i) bound[i] = (int)std::ceil(gmax * norm3(S.A[i]) / (2.0 * kPi)) + 1;
+  for (int a = -bound[0]; a <= bound[0]; ++a)
+    for (int b = -bound[1]; b <= bound[1]; ++b)
+      for (int c = -bound[2]; c <= bound[2]; ++c) {
+        double kg[3];
+        for (int d = 0; d < 3; ++d) kg[d] = kcart[d] + (a * S.B[0][d] + b * S.B[1][d] + c * S.B[2][d]);
+        if (0.5 * (kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]) <= ecut) out.push_back({a, b, c});
+      }
+  for (auto& m : out)
+    for (int i = 0; i < 3; ++i)
+      if (std::abs(m[i]) > (n - 1) / 2) return false;
+  return true;
+}
+
 static int fft_rep(int m, int n) { return m <= (n - 1) / 2 ? m : m - n; }
 
 std::string build_setup(const tc_params& p, Setup& S) {
@@ -284,20 +304,8 @@ std::string build_setup(const tc_params& p, Setup& S) {
   S.miller.assign(S.Nk, {});
   S.npw.assign(S.Nk, 0);
   for (int k = 0; k < S.Nk; ++k) {
-    const double gmax = std::sqrt(2.0 * p.ecut_ha) + norm3(S.kcart[k].data());
-    int bound[3];
-    for (int i = 0; i < 3; ++i) bound[i] = (int)std::ceil(gmax * norm3(S.A[i]) / (2.0 * kPi)) + 1;
-    for (int a = -bound[0]; a <= bound[0]; ++a)
-      for (int b = -bound[1]; b <= bound[1]; ++b)
-        for (int c = -bound[2]; c <= bound[2]; ++c) {
-          double kg[3];
-          for (int d = 0; d < 3; ++d) kg[d] = S.kcart[k][d] + (a * S.B[0][d] + b * S.B[1][d] + c * S.B[2][d]);
-          if (0.5 * (kg[0] * kg[0] + kg[1] * kg[1] + kg[2] * kg[2]) <= p.ecut_ha) S.miller[k].push_back({a, b, c});
-        }
+    if (!sphere(S, S.kcart[k].data(), S.miller[k])) return "plane-wave sphere does not fit the FFT box";
     S.npw[k] = (int)S.miller[k].size();
-    for (auto& m : S.miller[k])
-      for (int i = 0; i < 3; ++i)
-        if (std::abs(m[i]) > (n - 1) / 2) return "plane-wave sphere does not fit the FFT box";
   }
   S.npw_max = *std::max_element(S.npw.begin(), S.npw.end());
   S.miller_flat.assign((size_t)S.Nk * S.npw_max * 3, 0);

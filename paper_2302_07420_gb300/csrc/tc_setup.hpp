@@ -57,6 +57,11 @@ std::string build_setup(const tc_params& p, Setup& S);
 // Returns false when some k - q + G vanishes (k on the mesh).
 bool band_constants(const Setup& S, const double kcart[3], double* gamma_b, double W[3]);
 
+// The plane-wave sphere |k + m.B|^2/2 <= ecut of the wave vector kcart, Miller vectors m in
+// lexicographic order (the order of every sphere of the library).  Returns false when a vector
+// does not fit the FFT box (|m_i| > (n - 1)/2).  S needs only the lattice and the parameters.
+bool sphere(const Setup& S, const double kcart[3], std::vector<std::array<int, 3>>& out);
+
 // Appendix B kernel pieces (host, FP64), exposed for the table tests.
 double host_u_tilde(double p2, double A, double C);
 double host_gradu_sq(double p, double A, double C);

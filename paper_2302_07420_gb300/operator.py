@@ -268,6 +268,23 @@ def band_constants(lattice, kmesh, ecut, fft, nbands, nocc, A, C, kfrac_band, al
     return g, W
 
 
+def band_layout(lattice, kmesh, ecut, fft, nbands, nocc, A, C, kfrac_band):
+    """tc_band_layout: (npw (nkb,), miller (nkb, max npw, 3)) of the spheres at band points kfrac_band."""
+    lib = _lib.load()
+    prm = _lib.make_params(lattice, kmesh, ecut, fft, nbands, nocc, A, C)
+    kf = np.ascontiguousarray(np.atleast_2d(kfrac_band), dtype=np.float64)
+    n = kf.shape[0]
+    npw = np.zeros(n, dtype=np.int32)
+    dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    _lib.check(lib, None, lib.tc_band_layout(ctypes.byref(prm), kf.ctypes.data_as(dp), n, 0, npw.ctypes.data_as(ip),
+                                             None))
+    m = max(int(npw.max()) if n else 0, 1)
+    miller = np.zeros((n, m, 3), dtype=np.int32)
+    _lib.check(lib, None, lib.tc_band_layout(ctypes.byref(prm), kf.ctypes.data_as(dp), n, m, npw.ctypes.data_as(ip),
+                                             miller.ctypes.data_as(ip)))
+    return npw, miller
+
+
 class BatchContext:
     """tc_init_batch: many independent cells sharing one workspace, applied by one graph launch.
 
