@@ -100,8 +100,16 @@ typedef struct {
 
 typedef struct tc_ctx tc_ctx;
 
-/* Builds cell, k mesh, spheres, box maps, kernel tables (FP64 on the host) and
- * allocates all device workspace on the current CUDA device. */
+/* Builds cell, Gamma-centred k mesh and plane-wave spheres (Sec. 2.3), box
+ * maps, the FP64 kernel tables of V_2a, V_2a^dagger and u~ at every distinct
+ * k - q + G (Sec. 2.6.3, Appendix B) and the divergence-correction constant
+ * Gamma0 (Eq. correction2, Sec. 2.5) on the host, then uploads them and
+ * allocates all device workspace on the current CUDA device (tc_apply and
+ * tc_energy allocate nothing).  *out is owned by the caller and released by
+ * tc_destroy.  Errors (reason in tc_last_error(NULL), *out = NULL):
+ * TC_ERR_ARG (invalid parameters, a sphere that does not fit the box),
+ * TC_ERR_UNSUPPORTED (box size without a compiled specialisation, non-cubic
+ * box), TC_ERR_OOM (device allocation), TC_ERR_CUDA. */
 tc_status tc_init(const tc_params* params, tc_ctx** out);
 
 /* Basis layout.  *npw_per_k -> [Nk] ints, *miller -> [Nk][npw_max][3] ints
