@@ -342,21 +342,6 @@ size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max) {
 // Number of partner chunks s for a launch of `items` CTA items (per chunk one CTA): the s
 // (1 <= s <= min(8, partners)) that fills the last wave of CTAs over the SMs best, the
 // smallest such s when several are within 1 %.
-static int pick_split(int items, int partners, int sms) {
-  int best = 1;
-  double best_eff = 0.0;
-  for (int s = 1; s <= std::min(8, partners); ++s) {
-    const long long ctas = (long long)items * s;
-    const long long waves = (ctas + sms - 1) / sms;
-    const double eff = (double)ctas / (double)(waves * sms);
-    if (eff > best_eff + 0.01) {
-      best_eff = eff;
-      best = s;
-    }
-  }
-  return best;
-}
-
 void choose_splits(tc_ctx* c) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || sms <= 0) {
@@ -1025,18 +1010,8 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
       t_chain[s] = c->stage_ms[3] + c->stage_ms[4];
     }
     if (rs != TC_OK) break;
-    // the smallest count within 2 % of the fastest: near-ties between counts go the same way
-    // from run to run, and fewer chunks mean fewer partial sums
-    double b_occ = 1e300, b_chain = 1e300;
-    for (int s = 1; s <= smax; ++s) {
-      b_occ = std::min(b_occ, t_occ[s]);
-      b_chain = std::min(b_chain, t_chain[s]);
-    }
-    so[nsides - 1] = sc[nsides - 1] = 0;
-    for (int s = 1; s <= smax; ++s) {
-      if (!so[nsides - 1] && t_occ[s] <= 1.02 * b_occ) so[nsides - 1] = s;
-      if (!sc[nsides - 1] && t_chain[s] <= 1.02 * b_chain) sc[nsides - 1] = s;
-    }
+    so[nsides - 1] = tc::smallest_near_best(t_occ, smax);
+    sc[nsides - 1] = tc::smallest_near_best(t_chain, smax);
   }
   tc_profile(c, prof_was ? 1 : 0);
   c->split_occ[0] = so[0];

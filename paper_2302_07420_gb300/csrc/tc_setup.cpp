@@ -255,6 +255,29 @@ bool sphere(const Setup& S, const double kcart[3], std::vector<std::array<int, 3
   return true;
 }
 
+int pick_split(int items, int partners, int sms) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= std::min(8, partners); ++s) {
+    const long long ctas = (long long)items * s;
+    const long long waves = (ctas + sms - 1) / sms;
+    const double eff = (double)ctas / (double)(waves * sms);
+    if (eff > best_eff + 0.01) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
+}
+
+int smallest_near_best(const double* t, int n) {
+  double best = 1e300;
+  for (int s = 1; s <= n; ++s) best = std::min(best, t[s]);
+  for (int s = 1; s <= n; ++s)
+    if (t[s] <= 1.02 * best) return s;
+  return 1;
+}
+
 static int fft_rep(int m, int n) { return m <= (n - 1) / 2 ? m : m - n; }
 
 std::string build_setup(const tc_params& p, Setup& S) {

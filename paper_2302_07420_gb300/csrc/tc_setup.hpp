@@ -62,6 +62,13 @@ bool band_constants(const Setup& S, const double kcart[3], double* gamma_b, doub
 // does not fit the FFT box (|m_i| > (n - 1)/2).  S needs only the lattice and the parameters.
 bool sphere(const Setup& S, const double kcart[3], std::vector<std::array<int, 3>>& out);
 
+// Default partner chunks per CTA item: the s in 1 .. min(8, partners) whose launch of items x s CTAs
+// fills its last wave on `sms` SMs best (a larger s must raise the filled fraction by more than 1 %).
+int pick_split(int items, int partners, int sms);
+// The autotuner's rule over measured times t[1..n]: the smallest s within 2 % of the fastest, so that
+// near-ties go the same way from run to run and fewer chunks (fewer partial sums) win them.
+int smallest_near_best(const double* t, int n);
+
 // Appendix B kernel pieces (host, FP64), exposed for the table tests.
 double host_u_tilde(double p2, double A, double C);
 double host_gradu_sq(double p, double A, double C);
