@@ -66,7 +66,19 @@ typedef enum {
                               eigen-solver without convergence); outputs undefined */
 } tc_status;
 
-enum { TC_FP64 = 0, TC_FP32 = 1 };
+/* Precision of the FFTs and pair products (the energy sums, overlaps and divergence-correction
+ * scalars are FP64 in every mode; Sec. 2.6 prints no precision, the FP64 path is the reference).
+ *   TC_FP64        FP64 fields and transforms.
+ *   TC_FP32        FP32 fields and transforms, FP32 accumulation (in L2 reductions, fixed order).
+ *   TC_FP32_COMP   FP32 with compensated accumulation: not built, tc_init returns
+ *                  TC_ERR_UNSUPPORTED (plain FP32 accumulation already meets the 1e-5 bound of
+ *                  the operator output with a wide margin).
+ *   TC_BF16_STORE  TC_FP32 with the real-space orbital fields (phi, chi and their gradients,
+ *                  the operands of every pair density) rounded to BF16 (8-bit mantissa,
+ *                  round to nearest even) when they are stored; they are held in FP32 words and
+ *                  every product, transform and sum runs in FP32.  Its error (about 2^-9 per
+ *                  field value) is reported against FP64; it does not meet the 1e-5 bound. */
+enum { TC_FP64 = 0, TC_FP32 = 1, TC_FP32_COMP = 2, TC_BF16_STORE = 3 };
 
 /* Term indices of the operator (Sec. 2.6.3-2.6.4) and of E_terms.  The
  * three-body outputs include their multiplicities: 3a3 and 3a4 twice (3a6 = 3a3,
@@ -94,7 +106,7 @@ typedef struct {
   int div_correction;     /* 1: add the SCF-mesh divergence corrections (default) */
   double ushort_factor;   /* factor on the u_short terms of Eqs. divcor_3a2_first and
                              3b6_div_scf1; 1 reproduces the printed equations */
-  int precision;          /* TC_FP64 or TC_FP32 (FFTs and pair products) */
+  int precision;          /* TC_FP64, TC_FP32 or TC_BF16_STORE (TC_FP32_COMP: unsupported) */
   unsigned int term_mask; /* bit t enables operator term t; 0 enables all */
 } tc_params;
 

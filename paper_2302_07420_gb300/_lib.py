@@ -12,7 +12,8 @@ LIB_PATH = os.path.join(HERE, "libtc.so")
 
 (TC_OK, TC_ERR_ARG, TC_ERR_STATE, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED,
  TC_ERR_NUMERIC) = range(8)
-TC_FP64, TC_FP32 = 0, 1
+TC_FP64, TC_FP32, TC_FP32_COMP, TC_BF16_STORE = 0, 1, 2, 3
+PRECISIONS = {"fp64": TC_FP64, "fp32": TC_FP32, "fp32_comp": TC_FP32_COMP, "bf16_store": TC_BF16_STORE}
 TERMS = ("2ah", "2bh1", "2bh2", "2ax", "2bx1", "2bx2", "3a1", "3a2", "3a3", "3a4",
          "3b1", "3b2", "3b3", "3b4", "3b5", "3b6")
 TC_NTERMS = 17          # 16 operator terms + kinetic
@@ -119,7 +120,7 @@ def make_params(lattice, kmesh, ecut, fft, nbands, nocc, A, C, alpha=0.0, div_co
     p.alpha = float(alpha)
     p.div_correction = int(div_correction)
     p.ushort_factor = float(ushort_factor)
-    p.precision = TC_FP64 if precision in ("fp64", TC_FP64) else TC_FP32
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.term_mask = int(term_mask)
     return p
 

@@ -409,22 +409,11 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
   }
   tc::Setup& S = c->S;
   {
-    // the left/right conjugation of the occupied-pair fields holds on the grid for odd boxes, or
-    // when no pair density reaches the Nyquist plane (Miller span of all spheres <= n/2 - 1)
-    bool clear = S.n % 2 == 1;
-    if (!clear) {
-      clear = true;
-      for (int i = 0; i < 3; ++i) {
-        int lo = 1 << 30, hi = -(1 << 30);
-        for (int k = 0; k < S.Nk; ++k)
-          for (int g = 0; g < S.npw[k]; ++g) {
-            lo = std::min(lo, S.miller[k][g][i]);
-            hi = std::max(hi, S.miller[k][g][i]);
-          }
-        if (hi - lo > S.n / 2 - 1) clear = false;
-      }
-    }
-    c->left_from_right = clear;
+    // the left/right conjugation of the occupied-pair fields and the pruned pair-chain transforms
+    // both depend on how far the pair-density spectra reach on the box
+    const int span = tc::miller_span(S.miller);
+    c->left_from_right = tc::left_from_right_exact(S.n, span);
+    c->pair_support = tc::pair_support_len(S.n, span);
   }
   if (const int f = injected_fault("alloc")) {
     err = "injected fault (TC_FAULT=alloc): no device memory allocated";

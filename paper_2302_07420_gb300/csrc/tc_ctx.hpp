@@ -74,6 +74,9 @@ struct tc_ctx {
   // two-sided launches derive the left occupied-pair fields from the right ones (exact here:
   // odd box, or pair densities clear of the Nyquist planes)
   bool left_from_right = false;
+  // box indices per axis that a pair-density spectrum can occupy (tc::pair_support_len); the pair
+  // chains use their pruned transforms when it fits the compiled support length (large: never)
+  int pair_support = 1 << 30;
   // when set for one launch: a context with the same partners (occupied bands, occupations, cell,
   // precision) whose last launch left its partner-only fields (densities, Hartree-type fields,
   // occupied-pair stage) for the same sides; they are copied instead of recomputed

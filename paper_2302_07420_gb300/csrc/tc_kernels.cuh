@@ -1,5 +1,7 @@
 // Device-side parameter blocks of the TC operator kernels.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "tc_fft.cuh"
 
 namespace tc {

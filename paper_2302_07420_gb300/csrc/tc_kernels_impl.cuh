@@ -155,6 +155,17 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
               [&](int a, int b, int cc, cplx<T> v) { dst[G::gidx(a, b, cc)] = v; });
 }
 
+// BF16 storage (TC_BF16_STORE): every value of a[0 .. n) rounded to the nearest BF16 (ties to even),
+// kept in its FP32 word.
+template <typename T> __global__ void k_round_bf16(cplx<T>* a, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cplx<T> v = a[i];
+    v.x = (T)__bfloat162float(__float2bfloat16_rn((float)v.x));
+    v.y = (T)__bfloat162float(__float2bfloat16_rn((float)v.y));
+    a[i] = v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Densities of both sides: n = (1/Nk) sum_{k, mu < no} f conj(bra) ket, m likewise with grad ket.
 template <typename T, int N> __global__ void k_density(Params<T> P) {

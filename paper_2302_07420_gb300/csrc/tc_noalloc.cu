@@ -154,6 +154,12 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   c.device = dev;
+  {
+    // the same grid rules as tc_init: derived left occupied-pair fields, pruned pair chains
+    const int span = tc::miller_span(S.miller);
+    c.left_from_right = tc::left_from_right_exact(S.n, span);
+    c.pair_support = tc::pair_support_len(S.n, span);
+  }
   tc::choose_splits(&c);
   Layout L = plan(c, rsz);
   if (L.total > kNoallocBytes) {   // partner chunks multiply the accumulators: fall back to one chunk

@@ -6,6 +6,7 @@
 
 #include "tc_ctx.hpp"
 #include "tc_kernels_impl.cuh"
+#include "tc_pruned.cuh"
 
 namespace tc {
 
@@ -119,6 +120,10 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
   TC_SET_SMEM((k_occ_pairs<T, N>), (smem_vols<T, N>(4) * vb));
   TC_SET_SMEM((k_pair_chain<T, N>), (smem_vols<T, N>(3) * vb));
   TC_SET_SMEM((k_pair_3b4<T, N>), (smem_vols<T, N>(2) * vb));
+  if constexpr (kPruneL<N> < N) {
+    TC_SET_SMEM((k_pair_chain_pr<T, N, kPruneL<N>>), (int)(PrSmem<T, N, kPruneL<N>, 2, 3>::bytes));
+    TC_SET_SMEM((k_pair_3b4_pr<T, N, kPruneL<N>>), (int)(PrSmem<T, N, kPruneL<N>, 1, 1>::bytes));
+  }
   TC_SET_SMEM((k_fft3d<T, N, -1>), vb1);
   TC_SET_SMEM((k_fft3d<T, N, +1>), vb1);
   return TC_OK;
@@ -185,6 +190,15 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
                                                    (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi,
                                                    (cplx<T>*)ctx->d_scratch);
   TC_CHECK_LAUNCH("k_orbitals");
+  if (sizeof(T) == 4 && S.prm.precision == TC_BF16_STORE) {
+    const size_t no = (size_t)nj * S.N;   // orbitals x box points per set
+    k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_phi, no);
+    k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_chi, no);
+    k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_gphi, 3 * no);
+    k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_gchi, 3 * no);
+    TC_CHECK_LAUNCH("k_round_bf16");
+    nl[0] += 4;
+  }
   const tc_ctx* src = ctx->partners_from;
   if (src) {
     // stages 2 and 3 up to the local potential from a context with the same partners: the 25
@@ -272,10 +286,18 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   // 4. pair chains (with symmetry: output orbitals of irreducible k-points only)
   stage_mark(ctx, st, 3);
   const int nj_items = P.sym ? P.nirr * S.nb : nj;
+  // pair densities whose spectra fit the compiled support take the pruned transforms
+  constexpr int LP = kPruneL<N>;
+  const bool pruned = LP < N && ctx->pair_support <= LP;
   {
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);
-    k_pair_chain<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
+    if constexpr (LP < N) {
+      if (pruned)
+        k_pair_chain_pr<T, N, LP><<<dim3(nj_items * P.sc, nsides), PrCfg<T, N>::threads,
+                                    PrSmem<T, N, LP, 2, 3>::bytes, st>>>(Pc);
+    }
+    if (!pruned) k_pair_chain<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
     TC_CHECK_LAUNCH("k_pair_chain");
     stage_mark(ctx, st, 4);
     if (P.sc > 1) {
@@ -285,7 +307,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     }
     Params<T> Pb = P;
     Pb.nsmem = smem_vols<T, N>(2);
-    k_pair_3b4<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
+    if constexpr (LP < N) {
+      if (pruned)
+        k_pair_3b4_pr<T, N, LP><<<dim3(nj_items * P.sc, nsides), PrCfg<T, N>::threads,
+                                  PrSmem<T, N, LP, 1, 1>::bytes, st>>>(Pb);
+    }
+    if (!pruned) k_pair_3b4<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
     TC_CHECK_LAUNCH("k_pair_3b4");
     if (P.sc > 1 && tw[T3B4] != 0) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 2);

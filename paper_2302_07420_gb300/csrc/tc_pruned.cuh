@@ -1,0 +1,457 @@
+// Pair chains with pruned transforms (templated on precision T, box size N and support length L).
+//
+// Every transform of a pair chain has its spectrum on the support of the pair densities: the
+// forward transform of a pair density chi_q^* phi_j has nonzero coefficients only at m_j - m_q
+// (sphere Miller vectors, cyclic on the box), and every spectral accumulator of the chain is
+// consumed only through ket_q FT^{-1}[.], whose projection onto the sphere of k_j reads it at those
+// same indices.  When the Miller span s of all spheres satisfies 2 s + 1 <= L, the support per axis
+// lies in the L box indices {0 .. (L-1)/2} U {N - (L-1)/2 .. N-1}, so
+//   * an inverse transform reads L^3 spectral values: the axis-2 pass runs over L^2 pencils with
+//     L nonzero inputs each, the axis-3 pass over L N pencils with L nonzero inputs, and only the
+//     axis-1 pass produces the full N^3 real-space values;
+//   * a forward transform keeps L outputs per pencil in the same passes in reverse order;
+//   * the pair spectrum A and the spectral accumulator C are stored compactly ([L]^3), next to the
+//     work volume [L][N][N|1] (first index: compact axis-1 index) in shared memory.
+// This is exact for the discrete operator (the dropped coefficients are zero there).  Compact
+// index c maps to box index box(c) = c for c < (L+1)/2 and c + N - L otherwise; L = N means no
+// pruning (box(c) = c).
+#pragma once
+#include "tc_kernels.cuh"
+
+namespace tc {
+
+template <int N, int L> struct Sup {
+  static_assert(L <= N, "support longer than the box");
+  static constexpr int H = (L == N) ? N : (L + 1) / 2;
+  static constexpr int P = N | 1;              // row pitch of the work volume
+  static constexpr int bvol = L * N * P;       // work volume [L][N][P]
+  static constexpr int cvol = L * L * L;       // compact spectrum [L][L][L]
+  static __host__ __device__ constexpr int box(int c) { return c < H ? c : c + N - L; }
+  // Miller integer of compact index c
+  static __host__ __device__ constexpr int mil(int c) {
+    return (L == N) ? (c <= (N - 1) / 2 ? c : c - N) : (c < H ? c : c - L);
+  }
+  static __device__ __forceinline__ int bidx(int c1, int i2, int i3) { return (c1 * N + i2) * P + i3; }
+  static __device__ __forceinline__ int cidx(int c1, int c2, int c3) { return (c1 * L + c2) * L + c3; }
+};
+
+// Support length of the pruned kernels compiled for box size N (N: not compiled pruned).
+template <int N> constexpr int kPruneL = (N == 24) ? 17 : N;
+
+// Threads per CTA of the pruned kernels: one axis-1 pencil per thread in FP32, two in FP64
+// (a pencil of N double-complex values takes 4 N registers).
+template <typename T, int N> struct PrCfg {
+  static constexpr int threads = sizeof(T) == 4 ? ((N * N + 31) / 32) * 32 : ((N * N / 2 + 31) / 32) * 32;
+};
+
+// Shared-memory plan: work volume B first; the compact spectra A and C and the three kernel tables
+// of the current Delta (U_pp, U_ap, V on the support) follow when they fit, else A and C live in a
+// per-CTA slice of the global scratch and the tables are read from the full-box tables.
+template <typename T, int N, int L, int NSPEC, int NTAB> struct PrSmem {
+  using S = Sup<N, L>;
+  static constexpr size_t bB = (size_t)S::bvol * sizeof(cplx<T>);
+  static constexpr size_t bC = (size_t)S::cvol * sizeof(cplx<T>);
+  static constexpr size_t bT = (size_t)S::cvol * sizeof(T);
+  static constexpr size_t lim = (size_t)kSmemLimit - 1024;
+  static constexpr bool spec = bB + NSPEC * bC <= lim;
+  static constexpr bool tab = spec && bB + NSPEC * bC + NTAB * bT <= lim;
+  static constexpr size_t bytes = bB + (spec ? NSPEC * bC : 0) + (tab ? NTAB * bT : 0);
+};
+
+// *p += v in L2 without a return value; FP32 complex as one vector reduction.
+__device__ __forceinline__ void red_add_v(cplx<float>* p, cplx<float> v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void red_add_v(cplx<double>* p, cplx<double> v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+// Inverse transform, axes 2 and 3, of a compact spectrum spec(c1, c2, c3) into the work volume.
+template <typename T, int N, int L, typename Spec>
+__device__ __forceinline__ void pinv_23(cplx<T>* B, Spec spec) {
+  using S = Sup<N, L>;
+  for (int p = threadIdx.x; p < L * L; p += blockDim.x) {
+    const int c1 = p / L, c3 = p % L;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = cplx<T>{0, 0};
+#pragma unroll
+    for (int c2 = 0; c2 < L; ++c2) v[S::box(c2)] = spec(c1, c2, c3);
+    Codelet<T, N, +1>::run(v);
+#pragma unroll
+    for (int i2 = 0; i2 < N; ++i2) B[S::bidx(c1, i2, c3)] = v[i2];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < L * N; p += blockDim.x) {
+    const int c1 = p / N, i2 = p % N;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = cplx<T>{0, 0};
+#pragma unroll
+    for (int c3 = 0; c3 < L; ++c3) v[S::box(c3)] = B[S::bidx(c1, i2, c3)];
+    Codelet<T, N, +1>::run(v);
+#pragma unroll
+    for (int i3 = 0; i3 < N; ++i3) B[S::bidx(c1, i2, i3)] = v[i3];
+  }
+  __syncthreads();
+}
+
+// Axis-1 pass over the N^2 pencils (i2, i3).  FROM_B: the pencil's L spectral values are read from
+// the work volume and inverse-transformed (else load(i1, i2, i3) supplies N real-space values);
+// body(i2, i3, v) then works on the N real-space values; with fwd the pencil is forward-transformed
+// and its L support values are written back into the work volume.
+template <typename T, int N, int L, bool FROM_B, typename Load, typename Body>
+__device__ __forceinline__ void pass_axis1(cplx<T>* B, Load load, Body body, bool fwd) {
+  using S = Sup<N, L>;
+  for (int p = threadIdx.x; p < N * N; p += blockDim.x) {
+    const int i2 = p / N, i3 = p % N;
+    cplx<T> v[N];
+    if constexpr (FROM_B) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] = cplx<T>{0, 0};
+#pragma unroll
+      for (int c1 = 0; c1 < L; ++c1) v[S::box(c1)] = B[S::bidx(c1, i2, i3)];
+      Codelet<T, N, +1>::run(v);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) v[i] = load(i, i2, i3);
+    }
+    body(i2, i3, v);
+    if (fwd) {
+      Codelet<T, N, -1>::run(v);
+#pragma unroll
+      for (int c1 = 0; c1 < L; ++c1) B[S::bidx(c1, i2, i3)] = v[S::box(c1)];
+    }
+  }
+  __syncthreads();
+}
+
+// Forward transform, axes 3 and 2, of the work volume (axis 1 done, L x N x N values) onto the
+// support; emit(c1, c2, c3, value) receives each of the L^3 outputs once, from the thread that owns
+// the compact pencil (c1, c3) -- the same thread that reads it in pinv_23.
+template <typename T, int N, int L, typename Emit>
+__device__ __forceinline__ void pfwd_32(cplx<T>* B, Emit emit) {
+  using S = Sup<N, L>;
+  for (int p = threadIdx.x; p < L * N; p += blockDim.x) {
+    const int c1 = p / N, i2 = p % N;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i3 = 0; i3 < N; ++i3) v[i3] = B[S::bidx(c1, i2, i3)];
+    Codelet<T, N, -1>::run(v);
+#pragma unroll
+    for (int c3 = 0; c3 < L; ++c3) B[S::bidx(c1, i2, c3)] = v[S::box(c3)];
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < L * L; p += blockDim.x) {
+    const int c1 = p / L, c3 = p % L;
+    cplx<T> v[N];
+#pragma unroll
+    for (int i2 = 0; i2 < N; ++i2) v[i2] = B[S::bidx(c1, i2, c3)];
+    Codelet<T, N, -1>::run(v);
+#pragma unroll
+    for (int c2 = 0; c2 < L; ++c2) emit(c1, c2, c3, v[S::box(c2)]);
+  }
+  __syncthreads();
+}
+
+// p_d = Delta_d + G_d at compact index (c1, c2, c3)
+template <typename T, int N, int L>
+__device__ __forceinline__ T pcomp_c(const PComp<T>& q, int c1, int c2, int c3) {
+  using S = Sup<N, L>;
+  return q.c0 + (T)S::mil(c1) * q.b1 + (T)S::mil(c2) * q.b2 + (T)S::mil(c3) * q.b3;
+}
+
+template <int N, int L> __device__ __forceinline__ int gidx_c(int c1, int c2, int c3) {
+  using S = Sup<N, L>;
+  return (S::box(c1) * N + S::box(c2)) * N + S::box(c3);
+}
+
+// Fused pair chains, pruned (same work, grid and accumulators as k_pair_chain):
+//   A  = FT[conj(bra_q) ket_j]                                          on the support
+//   for d: b = FT^{-1}[U^pp_d A];  acc += f Z(q)_d b;  w_d += f ket_q b   (2bx1, 3a4, 3a3's w_j)
+//          F = conj(bra_q) Y(j)_d - tw3b5 ket_j h3b(q)_d + tw3b6 n b;  C += -U^pp_d FT[F]
+//   for d: b = FT^{-1}[U^ap_d A];  C += -U^ap_d FT[tw3b6 n b]             (3b6, antiparallel)
+//   acc += f ket_q FT^{-1}[C - tw2ax V A]                                 (3b3, 2bx2, 3b5, 3b6, 2ax)
+// (Algs. 2, 5, 6, 9, 11, 12 and the 2bx terms of Sec. 2.6.3.)
+template <typename T, int N, int L>
+__global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Params<T> P) {
+  using G = Geo<N>;
+  using S = Sup<N, L>;
+  using SM = PrSmem<T, N, L, 2, 3>;
+  constexpr int CH = sizeof(T) == 4 ? 2 : 1;   // elements per load chunk of the pointwise pass
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ T red[32];
+  const SideArgs<T>& SD = P.side[blockIdx.y];
+  const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
+  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
+  cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* A;
+  if constexpr (SM::spec) {
+    A = B + S::bvol;
+  } else {
+    const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    A = P.scratch + cta * 2 * (size_t)S::cvol;
+  }
+  cplx<T>* C = A + S::cvol;
+  T* tU = SM::tab ? reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) + SM::bB + 2 * SM::bC) : nullptr;
+  const size_t NN = G::nn;
+  const cplx<T>* ketj = SD.ket + (size_t)j * NN;
+  const cplx<T>* Yj = SD.Y + (size_t)j * 3 * NN;
+  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + j) * NN;
+  cplx<T>* w = SD.w + ((size_t)chunk * nj + j) * 3 * NN;
+  const T* tw = P.tw;
+  const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
+  const bool need_z = tw[T2BX1] != T(0) || tw[T3A4] != T(0);
+  const bool need_y = tw[T3B3] != T(0) || tw[T2BX2] != T(0);
+  const bool need_pp = need_w || need_z || tw[T3B6] != T(0);
+  const bool need_F = need_y || tw[T3B5] != T(0) || tw[T3B6] != T(0);
+  const bool need_ap = tw[T3B6] != T(0);
+  const T t3b5 = tw[T3B5], t3b6 = tw[T3B6], t2ax = tw[T2AX];
+  for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
+    acc[r] = cplx<T>{0, 0};
+    for (int d = 0; d < 3; ++d) w[d * NN + r] = cplx<T>{0, 0};
+  }
+  int staged = -1;   // Delta whose kernel tables are in shared memory
+  for (int qi = qi_begin; qi < qi_end; ++qi) {
+    const int kq = qi / P.no, mu = qi % P.no;
+    const int q = kq * P.nb + mu;
+    const T f = (T)(P.occ[q] / P.Nk);
+    if (f == T(0)) continue;
+    const int did = P.delta_id[kj * P.Nk + kq];
+    const T* dl = P.delta + did * 3;
+    const T* Vt = SD.tabV + ((size_t)did * 2 + SD.side) * NN;
+    const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
+    const T* Uap = P.tabU + ((size_t)did * 2 + 1) * NN;
+    if constexpr (SM::tab) {
+      if (did != staged) {
+        // the previous pair's last reads of the tables ended before its closing barrier
+        for (int c = threadIdx.x; c < S::cvol; c += blockDim.x) {
+          const int g = gidx_c<N, L>(c / (L * L), (c / L) % L, c % L);
+          tU[c] = Upp[g];
+          tU[S::cvol + c] = Uap[g];
+          tU[2 * S::cvol + c] = Vt[g];
+        }
+        staged = did;   // first read after the barriers of the forward transform below
+      }
+    }
+    auto tab = [&](int which, int c1, int c2, int c3) -> T {
+      if constexpr (SM::tab) {
+        return tU[which * S::cvol + S::cidx(c1, c2, c3)];
+      } else {
+        const T* t = which == 0 ? Upp : (which == 1 ? Uap : Vt);
+        return t[gidx_c<N, L>(c1, c2, c3)];
+      }
+    };
+    const cplx<T>* braq = SD.bra + (size_t)q * NN;
+    const cplx<T>* ketq = SD.ket + (size_t)q * NN;
+    const cplx<T>* Zq = SD.Z + ((size_t)(kq * P.no + mu) * 3) * NN;
+    const cplx<T>* h3bq = SD.h3b + ((size_t)(kq * P.no + mu) * 3) * NN;
+    // A = FT[conj(bra_q) ket_j] on the support
+    pass_axis1<T, N, L, false>(
+        B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ketj + g), ldg(braq + g)); },
+        [&](int, int, cplx<T>(&)[N]) {}, true);
+    pfwd_32<T, N, L>(B, [&](int c1, int c2, int c3, cplx<T> v) { A[S::cidx(c1, c2, c3)] = P.invN * v; });
+    if (P.div && kq == kj && t3b6 != T(0)) {
+      // O_qj = A(0) and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G) for the 3b6 corrections
+      for (int s = 0; s < 2; ++s) {
+        T xr = 0, xi = 0;
+        for (int c = threadIdx.x; c < S::cvol; c += blockDim.x) {
+          const int c1 = c / (L * L), c2 = (c / L) % L, c3 = c % L;
+          const int a = S::box(c1), b = S::box(c2), e = S::box(c3);
+          const int gn = G::gidx((N - a) % N, (N - b) % N, (N - e) % N);
+          const cplx<T> t = P.hartUs[(size_t)s * NN + G::gidx(a, b, e)] * (A[c] * SD.nt[gn]);
+          xr += t.x;
+          xi += t.y;
+        }
+        const T sr = block_sum<T>(xr, red);
+        const T si = block_sum<T>(xi, red);
+        if (threadIdx.x == 0) {
+          double* cs = SD.cs + ((size_t)j * P.no + mu) * 6;
+          cs[2 + 2 * s] = sr;
+          cs[3 + 2 * s] = si;
+          if (s == 0) { cs[0] = A[0].x; cs[1] = A[0].y; }
+        }
+      }
+      __syncthreads();
+    }
+    for (int sp = 0; sp < 2; ++sp) {
+      if (sp == 0 && !(need_pp || need_F)) continue;
+      if (sp == 1 && !need_ap) continue;
+      for (int d = 0; d < 3; ++d) {
+        const bool first_C = (sp == 0 && d == 0);
+        const PComp<T> qd = pcomp_setup<T>(P, dl, d);
+        // b = FT^{-1}[U_d A]
+        pinv_23<T, N, L>(B, [&](int c1, int c2, int c3) {
+          return mul_si<T, 1>((pcomp_c<T, N, L>(qd, c1, c2, c3) * tab(sp, c1, c2, c3)) * A[S::cidx(c1, c2, c3)]);
+        });
+        const bool fwd = sp == 1 || need_F;
+        pass_axis1<T, N, L, true>(
+            B, [&](int, int, int) { return cplx<T>{0, 0}; },
+            [&](int i2, int i3, cplx<T>(&v)[N]) {
+              if (sp == 0) {
+#pragma unroll
+                for (int c0 = 0; c0 < N; c0 += CH) {
+                  cplx<T> lz[CH], lk[CH], ly[CH], lb[CH], lj[CH], lh[CH], ln[CH];
+#pragma unroll
+                  for (int u = 0; u < CH; ++u) {
+                    if (c0 + u >= N) continue;
+                    const int g = G::gidx(c0 + u, i2, i3);
+                    if (need_z) lz[u] = ldg(Zq + d * NN + g);
+                    lk[u] = ldg(ketq + g);
+                    if (need_F) {
+                      ly[u] = ldg(Yj + d * NN + g);
+                      lb[u] = ldg(braq + g);
+                      lj[u] = ldg(ketj + g);
+                      lh[u] = ldg(h3bq + d * NN + g);
+                      ln[u] = ldg(SD.n + g);
+                    }
+                  }
+#pragma unroll
+                  for (int u = 0; u < CH; ++u) {
+                    if (c0 + u >= N) continue;
+                    const int g = G::gidx(c0 + u, i2, i3);
+                    const cplx<T> bv = v[c0 + u];
+                    if (need_z) red_add_v(&acc[g], f * (lz[u] * bv));
+                    if (need_w) red_add_v(&w[d * NN + g], f * (lk[u] * bv));
+                    cplx<T> F = {0, 0};
+                    if (need_F) {
+                      if (need_y) F = mulc(ly[u], lb[u]);
+                      if (t3b5 != T(0)) F = F - t3b5 * (lj[u] * lh[u]);
+                      if (t3b6 != T(0)) F = F + t3b6 * (ln[u] * bv);
+                    }
+                    v[c0 + u] = F;
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[i] = t3b6 * (ldg(SD.n + G::gidx(i, i2, i3)) * v[i]);
+              }
+            },
+            fwd);
+        if (!fwd) continue;
+        // C += -U_d FT[F] = -i p_d u FT[F]
+        pfwd_32<T, N, L>(B, [&](int c1, int c2, int c3, cplx<T> v) {
+          const T k = pcomp_c<T, N, L>(qd, c1, c2, c3) * tab(sp, c1, c2, c3) * P.invN;
+          const cplx<T> t = mul_si<T, -1>(k * v);
+          const int s = S::cidx(c1, c2, c3);
+          C[s] = first_C ? t : C[s] + t;
+        });
+      }
+    }
+    const bool has_C = need_F || need_ap;
+    if (has_C || t2ax != T(0)) {
+      pinv_23<T, N, L>(B, [&](int c1, int c2, int c3) {
+        const int s = S::cidx(c1, c2, c3);
+        cplx<T> v = has_C ? C[s] : cplx<T>{0, 0};
+        if (t2ax != T(0)) v = v - (t2ax * tab(2, c1, c2, c3)) * A[s];
+        return v;
+      });
+      pass_axis1<T, N, L, true>(
+          B, [&](int, int, int) { return cplx<T>{0, 0}; },
+          [&](int i2, int i3, cplx<T>(&v)[N]) {
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 4) {
+              cplx<T> lk[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + u < N) lk[u] = ldg(ketq + G::gidx(c0 + u, i2, i3));
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (c0 + u < N) red_add_v(&acc[G::gidx(c0 + u, i2, i3)], f * (lk[u] * v[c0 + u]));
+            }
+          },
+          false);
+    }
+  }
+}
+
+// Pass 2 for 3b4 (Alg. 10), pruned: acc += tw3b4 f ket_q FT^{-1}[-U^pp . FT[-conj(bra_q) w_j]]
+// (same grid and accumulators as k_pair_3b4).
+template <typename T, int N, int L>
+__global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_3b4_pr(Params<T> P) {
+  using G = Geo<N>;
+  using S = Sup<N, L>;
+  using SM = PrSmem<T, N, L, 1, 1>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const SideArgs<T>& SD = P.side[blockIdx.y];
+  const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
+  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
+  cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* A;
+  if constexpr (SM::spec) {
+    A = B + S::bvol;
+  } else {
+    const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    A = P.scratch + cta * (size_t)S::cvol;
+  }
+  T* tU = SM::tab ? reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) + SM::bB + SM::bC) : nullptr;
+  const size_t NN = G::nn;
+  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + j) * NN;
+  const cplx<T>* w = SD.w + (size_t)j * 3 * NN;
+  const T t3b4 = P.tw[T3B4];
+  if (t3b4 == T(0)) return;
+  if (chunk > 0) {
+    for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) acc[r] = cplx<T>{0, 0};
+    __syncthreads();
+  }
+  int staged = -1;
+  for (int qi = qi_begin; qi < qi_end; ++qi) {
+    const int kq = qi / P.no, mu = qi % P.no;
+    const int q = kq * P.nb + mu;
+    const T f = (T)(P.occ[q] / P.Nk);
+    if (f == T(0)) continue;
+    const int did = P.delta_id[kj * P.Nk + kq];
+    const T* dl = P.delta + did * 3;
+    const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
+    if constexpr (SM::tab) {
+      if (did != staged) {
+        for (int c = threadIdx.x; c < S::cvol; c += blockDim.x)
+          tU[c] = Upp[gidx_c<N, L>(c / (L * L), (c / L) % L, c % L)];
+        staged = did;
+      }
+    }
+    auto tab = [&](int c1, int c2, int c3) -> T {
+      if constexpr (SM::tab) return tU[S::cidx(c1, c2, c3)];
+      else return Upp[gidx_c<N, L>(c1, c2, c3)];
+    };
+    const cplx<T>* braq = SD.bra + (size_t)q * NN;
+    const cplx<T>* ketq = SD.ket + (size_t)q * NN;
+    for (int d = 0; d < 3; ++d) {
+      const PComp<T> qd = pcomp_setup<T>(P, dl, d);
+      pass_axis1<T, N, L, false>(
+          B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(w + d * NN + g), ldg(braq + g)); },
+          [&](int, int, cplx<T>(&)[N]) {}, true);
+      // -U_d FT[-conj(bra_q) w_d] = +i p_d u FT[conj(bra_q) w_d]
+      pfwd_32<T, N, L>(B, [&](int c1, int c2, int c3, cplx<T> v) {
+        const T k = pcomp_c<T, N, L>(qd, c1, c2, c3) * tab(c1, c2, c3) * P.invN;
+        const cplx<T> t = mul_si<T, 1>(k * v);
+        const int s = S::cidx(c1, c2, c3);
+        A[s] = d == 0 ? t : A[s] + t;
+      });
+    }
+    const T fw = t3b4 * f;
+    pinv_23<T, N, L>(B, [&](int c1, int c2, int c3) { return A[S::cidx(c1, c2, c3)]; });
+    pass_axis1<T, N, L, true>(
+        B, [&](int, int, int) { return cplx<T>{0, 0}; },
+        [&](int i2, int i3, cplx<T>(&v)[N]) {
+#pragma unroll
+          for (int c0 = 0; c0 < N; c0 += 4) {
+            cplx<T> lk[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (c0 + u < N) lk[u] = ldg(ketq + G::gidx(c0 + u, i2, i3));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (c0 + u < N) red_add_v(&acc[G::gidx(c0 + u, i2, i3)], fw * (lk[u] * v[c0 + u]));
+          }
+        },
+        false);
+  }
+}
+
+}  // namespace tc

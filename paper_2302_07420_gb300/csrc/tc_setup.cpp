@@ -270,6 +270,24 @@ int pick_split(int items, int partners, int sms) {
   return best;
 }
 
+int miller_span(const std::vector<std::vector<std::array<int, 3>>>& miller) {
+  int span = 0;
+  for (int i = 0; i < 3; ++i) {
+    int lo = 1 << 30, hi = -(1 << 30);
+    for (const auto& sph : miller)
+      for (const auto& m : sph) {
+        lo = std::min(lo, m[i]);
+        hi = std::max(hi, m[i]);
+      }
+    if (hi >= lo) span = std::max(span, hi - lo);
+  }
+  return span;
+}
+
+bool left_from_right_exact(int n, int span) { return n % 2 == 1 || span <= n / 2 - 1; }
+
+int pair_support_len(int n, int span) { return std::min(n, 2 * span + 1); }
+
 int smallest_near_best(const double* t, int n) {
   double best = 1e300;
   for (int s = 1; s <= n; ++s) best = std::min(best, t[s]);
@@ -293,7 +311,9 @@ std::string build_setup(const tc_params& p, Setup& S) {
   if (!(p.ecut_ha > 0)) return "ecut_ha must be positive";
   if (!(p.C[0] > 0 && p.C[1] > 0)) return "Jastrow C must be positive";
   if (!(p.A[0] >= 0 && p.A[1] >= 0)) return "Jastrow A must be non-negative";
-  if (p.precision != TC_FP64 && p.precision != TC_FP32) return "precision must be TC_FP64 or TC_FP32";
+  if (p.precision == TC_FP32_COMP) return "unsupported: TC_FP32_COMP (compensated FP32 accumulation) is not built";
+  if (p.precision != TC_FP64 && p.precision != TC_FP32 && p.precision != TC_BF16_STORE)
+    return "precision must be TC_FP64, TC_FP32 or TC_BF16_STORE";
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) S.A[i][j] = p.lattice[i][j];
   S.Omega = std::fabs(det3(S.A));

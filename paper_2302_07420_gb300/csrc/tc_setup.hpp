@@ -69,6 +69,16 @@ int pick_split(int items, int partners, int sms);
 // near-ties go the same way from run to run and fewer chunks (fewer partial sums) win them.
 int smallest_near_best(const double* t, int n);
 
+// Largest per-axis Miller span (max - min over the union of all spheres): a pair density
+// chi_q^* phi_j has its spectrum at Miller differences -span .. span on each axis.
+int miller_span(const std::vector<std::vector<std::array<int, 3>>>& miller);
+// Whether the left occupied-pair fields are exactly the conjugates of the right ones on this grid
+// (see k_left_from_right): an odd box, or pair densities clear of the Nyquist planes (span <= n/2 - 1).
+bool left_from_right_exact(int n, int span);
+// Box indices per axis that a pair-density spectrum can occupy: min(n, 2 span + 1).  The pruned
+// transforms of the pair chains apply when this is at most their compiled support length.
+int pair_support_len(int n, int span);
+
 // Appendix B kernel pieces (host, FP64), exposed for the table tests.
 double host_u_tilde(double p2, double A, double C);
 double host_gradu_sq(double p, double A, double C);

@@ -1,8 +1,11 @@
 // Test probe of the library's launch-decomposition rules (csrc/tc_setup.cpp): reads lines
 //   split <items> <partners> <sms>         -> prints pick_split
 //   near <n> <t1> ... <tn>                  -> prints smallest_near_best
+//   span <count> <m1 m2 m3> x count         -> prints miller_span of one sphere of count vectors
+//   grid <n> <span>                          -> prints left_from_right_exact and pair_support_len
 // from standard input and prints one integer per line.
 #include <cstdio>
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -22,6 +25,20 @@ int main() {
       for (int s = 1; s <= n; ++s)
         if (std::scanf("%lf", &t[s]) != 1) return 2;
       std::printf("%d\n", tc::smallest_near_best(t.data(), n));
+    } else if (!std::strcmp(cmd, "span")) {
+      int count = 0;
+      if (std::scanf("%d", &count) != 1 || count < 0) return 2;
+      std::vector<std::vector<std::array<int, 3>>> miller(1);
+      for (int i = 0; i < count; ++i) {
+        std::array<int, 3> m{};
+        if (std::scanf("%d %d %d", &m[0], &m[1], &m[2]) != 3) return 2;
+        miller[0].push_back(m);
+      }
+      std::printf("%d\n", tc::miller_span(miller));
+    } else if (!std::strcmp(cmd, "grid")) {
+      int n = 0, span = 0;
+      if (std::scanf("%d %d", &n, &span) != 2) return 2;
+      std::printf("%d %d\n", tc::left_from_right_exact(n, span) ? 1 : 0, tc::pair_support_len(n, span));
     } else {
       return 2;
     }

@@ -1,7 +1,10 @@
 """Host logic of the launch decomposition (csrc/tc_setup.cpp), on the CPU: the default partner-chunk
-count (pick_split: best filled last wave of CTAs on the SMs) and the autotuner's choice among measured
-counts (smallest_near_best: the smallest count within 2 % of the fastest).  A probe compiled from the
-library's source answers queries; the expected values restate the two rules.
+count (pick_split: best filled last wave of CTAs on the SMs), the autotuner's choice among measured
+counts (smallest_near_best: the smallest count within 2 % of the fastest), and the grid rules that
+tc_init and tc_apply_noalloc share: the Miller span of the spheres, whether the left occupied-pair
+fields are exact conjugates of the right ones (odd box or span <= n/2 - 1), and the pair-density
+support length min(n, 2 span + 1) that selects the pruned pair-chain transforms.  A probe compiled
+from the library's source answers queries; the expected values restate the rules.
 """
 import math
 import os
@@ -66,3 +69,33 @@ def test_smallest_near_best(probe):
     got = probe(["near %d %s" % (len(t), " ".join("%.17g" % x for x in t)) for t in cases])
     assert got == [_near(t) for t in cases]
     assert got[-4] == 4 and got[-3] == 1 and got[-2] == 1 and got[-1] == 2   # 209.0 at s = 4; 216.5 is 3.6 % off
+
+
+def test_miller_span_of_oracle_spheres(probe):
+    """The span of the oracle's own spheres (si_k444 cell: 8, the 24^3 support edge 17) and of
+    Gamma-only HEG spheres (|n|^2 <= 16: span 8)."""
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from conftest import make_setup
+    from paper_2302_07420_gb300 import synth
+    lines, want = [], []
+    for p in (synth.si_params(kmesh=(1, 1, 2)), synth.WORKLOADS["heg_14"](),
+              synth.tiny_params(11, kmesh=(1, 1, 2), fft=(24,) * 3, ecut=6.0, nbands=3, nocc=2, scale=5.0)):
+        S = make_setup(p)
+        allm = np.concatenate(S.miller)
+        lines.append("span %d %s" % (len(allm), " ".join("%d %d %d" % tuple(m) for m in allm)))
+        want.append(int((allm.max(0) - allm.min(0)).max()))
+    assert probe(lines) == want
+    assert want[0] == 8 and want[1] == 8
+
+
+def test_grid_rules(probe):
+    cases = [(n, s) for n in (9, 12, 15, 16, 24, 25, 48) for s in range(0, 26)]
+    out = probe(["grid %d %d" % c for c in cases])
+    pairs = list(zip(out[0::2], out[1::2]))
+    for (n, s), (clear, sup) in zip(cases, pairs):
+        assert clear == int(n % 2 == 1 or s <= n // 2 - 1), (n, s)
+        assert sup == min(n, 2 * s + 1), (n, s)
+    # the si_k444 grid: span 8 on 24^3 is clear of the Nyquist planes and fills the 17-index support
+    assert pairs[cases.index((24, 8))] == (1, 17)
+    assert pairs[cases.index((24, 9))] == (1, 19) and pairs[cases.index((24, 12))] == (0, 24)

@@ -79,3 +79,29 @@ def test_injected_allocation_fault_without_gpu(lib, monkeypatch):
     assert not h.value
     bad = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], (10, 10, 10), 3, 2, p["A"], p["C"])
     assert lib.tc_init(ctypes.byref(bad), ctypes.byref(h)) == _lib.TC_ERR_UNSUPPORTED   # setup errors first
+
+
+def test_precision_modes_without_gpu(lib):
+    """TC_FP32_COMP (compensated accumulation, not built) is refused as unsupported by the host
+    setup; an unknown precision is an argument error; TC_BF16_STORE passes the setup (TC_FAULT=alloc
+    stops it before any device call)."""
+    import ctypes
+    from paper_2302_07420_gb300 import _lib, synth
+    p = synth.tiny_params(0, kmesh=(1, 1, 2), fft=(9, 9, 9), ecut=1.6, scale=5.0)
+    h = ctypes.c_void_p()
+    prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], 3, 2, p["A"], p["C"], precision="fp32_comp")
+    assert lib.tc_init(ctypes.byref(prm), ctypes.byref(h)) == _lib.TC_ERR_UNSUPPORTED
+    assert b"TC_FP32_COMP" in lib.tc_last_error(None)
+    prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], 3, 2, p["A"], p["C"], precision=9)
+    assert lib.tc_init(ctypes.byref(prm), ctypes.byref(h)) == _lib.TC_ERR_ARG
+    prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], 3, 2, p["A"], p["C"], precision="bf16_store")
+    import os as _os
+    old = _os.environ.get("TC_FAULT")
+    _os.environ["TC_FAULT"] = "alloc"
+    try:
+        assert lib.tc_init(ctypes.byref(prm), ctypes.byref(h)) == _lib.TC_ERR_OOM
+    finally:
+        if old is None:
+            del _os.environ["TC_FAULT"]
+        else:
+            _os.environ["TC_FAULT"] = old
