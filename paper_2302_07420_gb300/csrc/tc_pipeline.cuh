@@ -123,6 +123,7 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
   if constexpr (kPruneL<N> < N) {
     TC_SET_SMEM((k_pair_chain_pr<T, N, kPruneL<N>>), (int)(PrSmem<T, N, kPruneL<N>, 2, 3>::bytes));
     TC_SET_SMEM((k_pair_3b4_pr<T, N, kPruneL<N>>), (int)(PrSmem<T, N, kPruneL<N>, 1, 1>::bytes));
+    TC_SET_SMEM((k_occ_pairs_pr<T, N, kPruneL<N>>), (int)(OccSmem<T, N, kPruneL<N>>::bytes));
   }
   TC_SET_SMEM((k_fft3d<T, N, -1>), vb1);
   TC_SET_SMEM((k_fft3d<T, N, +1>), vb1);
@@ -183,6 +184,9 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   const int nj = S.Nk * S.nb;
   const int pw_blocks = 2 * 152;
   int nl[6] = {1, 9, 0, 1, 1, 1};   // kernel launches per stage
+  // pair densities whose spectra fit the compiled support take the pruned transforms
+  constexpr int LP = kPruneL<N>;
+  const bool pruned = LP < N && ctx->pair_support <= LP;
   // 1. orbitals to real space
   stage_mark(ctx, st, 0);
   k_orbitals<T, N><<<dim3(nj, 4, 2), TH, vb1, st>>>(cphi, cchi, ctx->d_box_index, ctx->d_kpg, S.npw_max, S.nb,
@@ -251,7 +255,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     Pa.nsmem = smem_vols<T, N>(4);
     if (derive_left) Pa.so = ctx->split_occ[0];
     const int q2_items = P.sym ? P.nirr * S.no : S.Nk * S.no;   // irreducible q2 only with symmetry
-    k_occ_pairs<T, N><<<dim3(q2_items * Pa.so, occ_sides), TH, Pa.nsmem * vb, st>>>(Pa);
+    if constexpr (LP < N) {
+      if (pruned)
+        k_occ_pairs_pr<T, N, LP><<<dim3(q2_items * Pa.so, occ_sides), PrCfg<T, N>::threads,
+                                   OccSmem<T, N, LP>::bytes, st>>>(Pa);
+    }
+    if (!pruned) k_occ_pairs<T, N><<<dim3(q2_items * Pa.so, occ_sides), TH, Pa.nsmem * vb, st>>>(Pa);
     TC_CHECK_LAUNCH("k_occ_pairs");
     if (Pa.so > 1) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, occ_sides), 256, 0, st>>>(Pa, 0);
@@ -286,9 +295,6 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   // 4. pair chains (with symmetry: output orbitals of irreducible k-points only)
   stage_mark(ctx, st, 3);
   const int nj_items = P.sym ? P.nirr * S.nb : nj;
-  // pair densities whose spectra fit the compiled support take the pruned transforms
-  constexpr int LP = kPruneL<N>;
-  const bool pruned = LP < N && ctx->pair_support <= LP;
   {
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);

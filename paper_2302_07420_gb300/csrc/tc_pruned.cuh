@@ -454,4 +454,182 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_3b4_pr(Params<
   }
 }
 
+// Occupied-pair stage, pruned (same grid, outputs and per-CTA h6 part as k_occ_pairs; Algs. 4, 6, 8,
+// 11 and the 3a2 corrections of Eqs. divcor_3a2_first/second in the general-overlap form):
+//   A1 = FT[conj(bra_q2) ket_q1], A2 = FT[conj(bra_q1) ket_q2]                      on the support
+//   B1 = P^s_d(q2, q1) = FT^{-1}[U^s_d(k1 - k2 + G) A1]   (real space, in shared memory)
+//   B2 = P^s_d(q1, q2) = FT^{-1}[U^s_d(k2 - k1 + G) A2]   (its last pass fused with the products)
+//   h6 += w f1 f2 B1 . B2;  h3a4(q2)_d += f1 B2 ket_q1;  h3b(q2)_d += f1 B1 conj(bra_q1)   (s = pp)
+// Shared memory: B1 as a real-space volume [N][N][N|1] (rows c1 < L serve as its inverse work
+// area), then the work volume of B2 [L][N][N|1] when it fits (FP32), else in the CTA's scratch
+// slice.  The compact spectra A1, A2 and the 3a2 spectrum F_ab live in the CTA's scratch slice
+// (slots 0, 1, 2; slot 4 is the h6 part that k_reduce_a4 sums, as for k_occ_pairs).
+template <typename T, int N, int L> struct OccSmem {
+  using S = Sup<N, L>;
+  static constexpr size_t bR = (size_t)Geo<N>::vol * sizeof(cplx<T>);
+  static constexpr size_t bW = (size_t)S::bvol * sizeof(cplx<T>);
+  static constexpr size_t lim = (size_t)kSmemLimit - 1024;
+  static constexpr bool w_smem = bR + bW <= lim;
+  static constexpr size_t bytes = bR + (w_smem ? bW : 0);
+};
+
+template <typename T, int N, int L>
+__global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params<T> P) {
+  using G = Geo<N>;
+  using S = Sup<N, L>;
+  using SM = OccSmem<T, N, L>;
+  static_assert(S::bvol <= G::vol && S::cvol <= G::vol, "slots hold a full volume");
+  constexpr int NS = 6;
+  constexpr int CH = sizeof(T) == 4 ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double sO[2][2];
+  __shared__ double sF0[2];
+  const SideArgs<T>& SD = P.side[blockIdx.y];
+  const int M = P.Nk * P.no;
+  const int item = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
+  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : item;
+  const int k2 = i2 / P.no, mu2 = i2 % P.no;
+  const int q2 = k2 * P.nb + mu2;
+  const int i1_begin = (int)((long long)chunk * M / P.so), i1_end = (int)((long long)(chunk + 1) * M / P.so);
+  const size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+  cplx<T>* slice = P.scratch + cta * NS * (size_t)G::vol;
+  cplx<T>* R1 = reinterpret_cast<cplx<T>*>(smraw);
+  cplx<T>* W2 = SM::w_smem ? R1 + G::vol : slice + 3 * (size_t)G::vol;
+  cplx<T>* A1 = slice;
+  cplx<T>* A2 = slice + G::vol;
+  cplx<T>* FAB = slice + 2 * (size_t)G::vol;
+  cplx<T>* H6 = slice + 4 * (size_t)G::vol;
+  const size_t NN = G::nn;
+  const T f2 = (T)(P.occ[q2] / P.Nk);
+  cplx<T>* h3a4 = SD.h3a4 + ((size_t)chunk * M + i2) * 3 * NN;
+  cplx<T>* h3b = SD.h3b + ((size_t)chunk * M + i2) * 3 * NN;
+  const cplx<T>* bra2 = SD.bra + (size_t)q2 * NN;
+  const cplx<T>* ket2 = SD.ket + (size_t)q2 * NN;
+  for (int r = threadIdx.x; r < S::cvol; r += blockDim.x) FAB[r] = cplx<T>{0, 0};
+  for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
+    H6[r] = cplx<T>{0, 0};
+    for (int d = 0; d < 3; ++d) {
+      h3a4[d * NN + r] = cplx<T>{0, 0};
+      h3b[d * NN + r] = cplx<T>{0, 0};
+    }
+  }
+  if (threadIdx.x == 0) { sF0[0] = 0.0; sF0[1] = 0.0; }
+  __syncthreads();
+  for (int i1 = i1_begin; i1 < i1_end; ++i1) {
+    const int k1 = i1 / P.no, mu1 = i1 % P.no;
+    const int q1 = k1 * P.nb + mu1;
+    const T f1 = (T)(P.occ[q1] / P.Nk);
+    if (f1 == T(0) || f2 == T(0)) continue;
+    const int id12 = P.delta_id[k2 * P.Nk + k1];   // Delta = k2 - k1 -> for P(q1,q2)
+    const int id21 = P.delta_id[k1 * P.Nk + k2];   // Delta = k1 - k2 -> for P(q2,q1)
+    const T* d12 = P.delta + id12 * 3;
+    const T* d21 = P.delta + id21 * 3;
+    const cplx<T>* bra1 = SD.bra + (size_t)q1 * NN;
+    const cplx<T>* ket1 = SD.ket + (size_t)q1 * NN;
+    // A1 = FT[conj(bra_q2) ket_q1], A2 = FT[conj(bra_q1) ket_q2] (work area: the rows of R1)
+    pass_axis1<T, N, L, false>(
+        R1, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ket1 + g), ldg(bra2 + g)); },
+        [&](int, int, cplx<T>(&)[N]) {}, true);
+    pfwd_32<T, N, L>(R1, [&](int c1, int c2, int c3, cplx<T> v) { A1[S::cidx(c1, c2, c3)] = P.invN * v; });
+    pass_axis1<T, N, L, false>(
+        R1, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ket2 + g), ldg(bra1 + g)); },
+        [&](int, int, cplx<T>(&)[N]) {}, true);
+    pfwd_32<T, N, L>(R1, [&](int c1, int c2, int c3, cplx<T> v) { A2[S::cidx(c1, c2, c3)] = P.invN * v; });
+    // 3a2 correction pieces for pairs at the same k (Eqs. divcor_3a2_*_density_matrix_mixing)
+    if (P.div && k1 == k2) {
+      if (threadIdx.x == 0) {
+        const cplx<T> o21 = A1[0], o12 = A2[0];   // <bra_q2|ket_q1>, <bra_q1|ket_q2>
+        sO[0][0] = o21.x; sO[0][1] = o21.y; sO[1][0] = o12.x; sO[1][1] = o12.y;
+        const double fq = P.occ[q1];
+        sF0[0] += fq * ((double)o21.x * o12.x - (double)o21.y * o12.y);
+        sF0[1] += fq * ((double)o21.x * o12.y + (double)o21.y * o12.x);
+      }
+      __syncthreads();
+      const cplx<T> o21 = {(T)sO[0][0], (T)sO[0][1]}, o12 = {(T)sO[1][0], (T)sO[1][1]};
+      const T fq = (T)P.occ[q1];
+      for (int r = threadIdx.x; r < S::cvol; r += blockDim.x) FAB[r] = FAB[r] + fq * (o12 * A1[r] + o21 * A2[r]);
+      __syncthreads();
+    }
+    // antiparallel channel: each unordered pair once (see k_occ_pairs)
+    const int cyc = (i1 - i2 + M) % M;
+    const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
+    const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
+    for (int sp = 0; sp < 2; ++sp) {
+      if (sp == 1 && !ap_here) continue;
+      const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
+      const T* U21 = P.tabU + ((size_t)id21 * 2 + sp) * NN;
+      const T* U12 = P.tabU + ((size_t)id12 * 2 + sp) * NN;
+      for (int d = 0; d < 3; ++d) {
+        const PComp<T> q21 = pcomp_setup<T>(P, d21, d), q12 = pcomp_setup<T>(P, d12, d);
+        // B1 = P^s_d(q2, q1), real space in R1
+        pinv_23<T, N, L>(R1, [&](int c1, int c2, int c3) {
+          const int s = S::cidx(c1, c2, c3);
+          return mul_si<T, 1>((pcomp_c<T, N, L>(q21, c1, c2, c3) * U21[gidx_c<N, L>(c1, c2, c3)]) * A1[s]);
+        });
+        pass_axis1<T, N, L, true>(
+            R1, [&](int, int, int) { return cplx<T>{0, 0}; },
+            [&](int a2, int a3, cplx<T>(&v)[N]) {
+#pragma unroll
+              for (int i = 0; i < N; ++i) R1[G::sidx(i, a2, a3)] = v[i];
+            },
+            false);
+        // B2 = P^s_d(q1, q2); its axis-1 pass forms the products with B1
+        pinv_23<T, N, L>(W2, [&](int c1, int c2, int c3) {
+          const int s = S::cidx(c1, c2, c3);
+          return mul_si<T, 1>((pcomp_c<T, N, L>(q12, c1, c2, c3) * U12[gidx_c<N, L>(c1, c2, c3)]) * A2[s]);
+        });
+        pass_axis1<T, N, L, true>(
+            W2, [&](int, int, int) { return cplx<T>{0, 0}; },
+            [&](int a2, int a3, cplx<T>(&v)[N]) {
+#pragma unroll
+              for (int c0 = 0; c0 < N; c0 += CH) {
+                cplx<T> lb1[CH], lk[CH], lr[CH];
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                  if (c0 + u >= N) continue;
+                  const int g = G::gidx(c0 + u, a2, a3);
+                  lb1[u] = R1[G::sidx(c0 + u, a2, a3)];
+                  if (sp == 0) {
+                    lk[u] = ldg(ket1 + g);
+                    lr[u] = ldg(bra1 + g);
+                  }
+                }
+#pragma unroll
+                for (int u = 0; u < CH; ++u) {
+                  if (c0 + u >= N) continue;
+                  const int g = G::gidx(c0 + u, a2, a3);
+                  const cplx<T> b2 = v[c0 + u];
+                  red_add_v(&H6[g], w12 * (lb1[u] * b2));
+                  if (sp == 0) {
+                    red_add_v(&h3a4[d * NN + g], f1 * (b2 * lk[u]));
+                    red_add_v(&h3b[d * NN + g], f1 * mulc(lb1[u], lr[u]));
+                  }
+                }
+              }
+            },
+            false);
+      }
+    }
+  }
+  // 3a2 corrections of this q2: (f2/Nk)/Omega^2 sum_s [c_s F0 + (4 pi A_s/Nk) FT^{-1}[u~_s F_ab]]
+  if (P.div && f2 != T(0)) {
+    const T pref = (T)(f2 * P.invOm2);
+    const T c0 = (T)(P.corr_c[0] + P.corr_c[1]);
+    const cplx<T> cF0 = {(T)(c0 * sF0[0]), (T)(c0 * sF0[1])};
+    const T a0 = (T)(4.0 * 3.14159265358979323846 * P.A[0] / P.Nk), a1 = (T)(4.0 * 3.14159265358979323846 * P.A[1] / P.Nk);
+    pinv_23<T, N, L>(W2, [&](int c1, int c2, int c3) {
+      const int g = gidx_c<N, L>(c1, c2, c3);
+      const T u = a0 * P.hartUs[g] + a1 * P.hartUs[NN + g];
+      return u * FAB[S::cidx(c1, c2, c3)];
+    });
+    pass_axis1<T, N, L, true>(
+        W2, [&](int, int, int) { return cplx<T>{0, 0}; },
+        [&](int a2, int a3, cplx<T>(&v)[N]) {
+#pragma unroll
+          for (int i = 0; i < N; ++i) red_add_v(&H6[G::gidx(i, a2, a3)], pref * (v[i] + cF0));
+        },
+        false);
+  }
+}
+
 }  // namespace tc
