@@ -302,6 +302,33 @@ tc_status tc_band_constants(const tc_params* params, const double* kfrac_band, i
 tc_status tc_band_layout(const tc_params* params, const double* kfrac_band, int nkb, int max_npw, int* npw,
                          int* miller);
 
+/* tc_init_band / tc_apply_band -- the operator at band-structure k-points off the SCF mesh
+ * (Sec. 2.6.3 after Eq. divcorr_2ax_scf; Sec. 2.6.4): output orbitals at nkb band points k_b,
+ * partners on the SCF mesh.  Every partner-only field (densities, Hartree-type fields, the
+ * occupied-pair stage with its 3a2 correction) is that of the SCF operator; the pair terms take
+ * their kernels at k_b - q + G; the divergence corrections are the band forms: Eq.
+ * divcorr_2ax_band and 3b6_div_band1/2/3 with Gamma_b, and the grad-u corrections of Eq.
+ * correction_nabla with W(k_b) (Eqs. divcorr_2bx1/2, divcorr_3a3, div_corr_3b3_2,
+ * div_corr_3a4_2/3, 3b5_div_2/3, div_corr_3b4_2/4), which use the band point's own occupied
+ * orbitals (the first nocc band-point orbitals, occupations band_occ) and their occupied-pair fields
+ * against the mesh partners (the constants are those of tc_band_constants).
+ *
+ * tc_init_band builds a context for params (the SCF mesh) and the band points kfrac_band
+ * ([nkb][3] fractional coordinates, host; every point off the mesh modulo a reciprocal vector,
+ * else TC_ERR_ARG).  Its tc_layout reports Nk + nkb k-points (the mesh, then the band points) and
+ * one npw_max for all of them: every orbital array of tc_apply_band uses that npw_max.
+ * tc_apply_band: phi_R, phi_L [Nk][nbands][npw_max] mesh orbitals (the partners, as tc_apply);
+ * occ host [Nk][nbands]; band_phi_R, band_phi_L [nkb][nbands][npw_max] band-point orbitals on
+ * their spheres (tc_band_layout order); band_occ host [nkb][nbands] (only the first nocc act, in
+ * the corrections); out_R, out_L [nkb][nbands][npw_max] = (h_2 + h_3) phi_b and (h_2 + h_3)^dagger
+ * chi_b at the band points (either may be NULL).  Device pointers only (TC_ERR_ARG otherwise); no
+ * allocation; not thread-safe per context.  Other operator calls on a band context (tc_apply,
+ * tc_energy, tc_energy_grad, tc_autotune, tc_biorthonormalize, tc_davidson_step, tc_set_symmetry)
+ * return TC_ERR_STATE. */
+tc_status tc_init_band(const tc_params* params, int nkb, const double* kfrac_band, tc_ctx** out);
+tc_status tc_apply_band(tc_ctx* ctx, const void* phi_R, const void* phi_L, const double* occ, const void* band_phi_R,
+                        const void* band_phi_L, const double* band_occ, void* out_R, void* out_L, void* cuda_stream);
+
 /* tc_alu_peak -- measured fused multiply-add throughput of the current
  * device's non-tensor pipes, the denominator of the roofline of the FFT and
  * pair-product kernels (the paper has no counterpart: a measurement helper of

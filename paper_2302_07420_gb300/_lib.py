@@ -21,7 +21,7 @@ EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy",
             "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
             "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
             "tc_davidson_step", "tc_set_symmetry", "tc_symmetry_info", "tc_symmetrize_orbitals", "tc_autotune",
-            "tc_alu_peak", "tc_band_constants", "tc_band_layout")
+            "tc_alu_peak", "tc_band_constants", "tc_band_layout", "tc_init_band", "tc_apply_band")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",
@@ -96,7 +96,9 @@ def load():
     lib.tc_alu_peak.argtypes = [ip, ctypes.c_double, dp, vp]
     lib.tc_band_constants.argtypes = [ctypes.POINTER(tc_params), dp, ip, dp, dp]
     lib.tc_band_layout.argtypes = [ctypes.POINTER(tc_params), dp, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
-    for name in ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
+    lib.tc_init_band.argtypes = [ctypes.POINTER(tc_params), ip, dp, ctypes.POINTER(vp)]
+    lib.tc_apply_band.argtypes = [vp, vp, vp, dp, vp, vp, dp, vp, vp, vp]
+    for name in ("tc_init_band", "tc_apply_band", "tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
                  "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
             "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
             "tc_davidson_step", "tc_set_symmetry", "tc_symmetry_info", "tc_symmetrize_orbitals", "tc_autotune",

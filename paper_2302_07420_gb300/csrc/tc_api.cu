@@ -47,6 +47,16 @@ int dispatch_run(tc_ctx* c, const double2* a, const double2* b, double2* oR, dou
   return TC_ERR_UNSUPPORTED;
 }
 
+template <typename T>
+int dispatch_run_band(tc_ctx* c, const double2* a, const double2* b, const double2* ba, const double2* bb, double2* oR,
+                      double2* oL, const double* tw, cudaStream_t st) {
+#define CASE(NN) \
+  case NN: return tc::run_pipeline<T, NN>(c, a, b, oR, oL, tw, 2, st, ba, bb);
+  switch (c->S.n) { TC_FOR_N(CASE) }
+#undef CASE
+  return TC_ERR_UNSUPPORTED;
+}
+
 template <typename T> int dispatch_fft(int n, void* data, int batch, int sign, cudaStream_t st) {
 #define CASE(NN) \
   case NN: return tc::run_fft3d<T, NN>(data, batch, sign, st);
@@ -86,7 +96,7 @@ template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t&
 void free_all(tc_ctx* c) {
   void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
                   c->d_hartU, c->d_hartUs, c->d_occ, c->ws_owned ? c->d_ws : nullptr, c->d_in_phi, c->d_in_chi,
-                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status};
+                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status, c->d_band, c->d_bs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
@@ -309,7 +319,7 @@ namespace tc {
 
 WsLayout ws_layout(const tc_ctx* c) {
   const Setup& S = c->S;
-  const size_t NN = (size_t)S.N, nj = (size_t)S.Nk * S.nb, vol = NN * c->esz;
+  const size_t NN = (size_t)S.N, nj = (size_t)S.Nkt * S.nb, vol = NN * c->esz;   // orbitals of all k-points
   WsLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -322,9 +332,9 @@ WsLayout ws_layout(const tc_ctx* c) {
   L.chi = take(nj * vol);
   L.gphi = take(nj * 3 * vol);
   L.gchi = take(nj * 3 * vol);
-  L.side_bytes = side_field_vols(S.Nk, S.nb, S.no, c->so_max, c->sc_max) * vol;
+  L.side_bytes = side_field_vols(S.Nk, S.nb, S.no, c->so_max, c->sc_max, c->nj_out, S.nkb, c->so_band) * vol;
   L.side = take(2 * L.side_bytes);
-  L.cs_bytes = (size_t)2 * nj * S.no * 6 * sizeof(double);
+  L.cs_bytes = (size_t)2 * c->nj_out * S.no * 6 * sizeof(double);
   L.cs = take(L.cs_bytes);
   L.scratch_bytes = c->prec == TC_FP64 ? dispatch_scratch<double>(S, S.n, c->so_max, c->sc_max)
                                        : dispatch_scratch<float>(S, S.n, c->so_max, c->sc_max);
@@ -333,10 +343,13 @@ WsLayout ws_layout(const tc_ctx* c) {
   return L;
 }
 
-size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max) {
+size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max, int nj_out, int nkb, int so_band) {
   // n, m(3), nt, mt(3), vH, h1(3), vb2, t3b1, t3b2, vu(2), spec(3), h5(3), h6, vloc = 25; per occupied
-  // state h3a4(3) and h3b(3) per chunk part and Z(3); per orbital acc(1) and w(3) per part and Y(3)
-  return 25 + (size_t)Nk * no * 3 * (2 * (size_t)so_max + 1) + (size_t)Nk * nb * (4 * (size_t)sc_max + 3);
+  // state h3a4(3) and h3b(3) per chunk part and Z(3); per output orbital acc(1) and w(3) per part and
+  // Y(3); with band points: V2 and V3 (4 per point) and both h3 kinds (3 each) of every band-point occupied
+  // orbital per band chunk part
+  return 25 + (size_t)Nk * no * 3 * (2 * (size_t)so_max + 1) + (size_t)nj_out * (4 * (size_t)sc_max + 3) +
+         (size_t)nkb * (4 + (size_t)no * 6 * so_band);
 }
 
 // Number of partner chunks s for a launch of `items` CTA items (per chunk one CTA): the s
@@ -349,13 +362,14 @@ void choose_splits(tc_ctx* c) {
     sms = 1;
   }
   const Setup& S = c->S;
-  const int M = S.Nk * S.no, nj = S.Nk * S.nb;
+  const int M = S.Nk * S.no, nj = c->nj_out;
   for (int sides = 1; sides <= 2; ++sides) {
     c->split_occ[sides - 1] = pick_split(M * sides, M, sms);
     c->split_chain[sides - 1] = pick_split(nj * sides, M, sms);
   }
   c->so_max = std::max(c->split_occ[0], c->split_occ[1]);
   c->sc_max = std::max(c->split_chain[0], c->split_chain[1]);
+  c->so_band = S.nkb > 0 ? pick_split(2 * S.nkb * S.no, M, sms) : 1;
 }
 
 int pick_split_for(int items, int partners, int device) {
@@ -397,17 +411,20 @@ void ws_assign(tc_ctx* c, char* base, const WsLayout& L) {
   c->scratch_bytes = L.scratch_bytes;
 }
 
-int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std::string& err) {
+int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std::string& err, int nkb,
+                 const double* kfrac_band) {
   *out = nullptr;
   tc_ctx* c = new (std::nothrow) tc_ctx();
   if (!c) { err = "host allocation failed"; return TC_ERR_OOM; }
   std::string why = tc::build_setup(*params, c->S);
+  if (why.empty() && nkb > 0) why = tc::add_band_points(c->S, nkb, kfrac_band);
   if (!why.empty()) {
     err = why;
     delete c;
     return why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG;
   }
   tc::Setup& S = c->S;
+  c->nj_out = (S.nkb > 0 ? S.nkb : S.Nk) * S.nb;
   {
     // the left/right conjugation of the occupied-pair fields and the pruned pair-chain transforms
     // both depend on how far the pair-density spectra reach on the box
@@ -431,8 +448,8 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
   // basis
   ok(cudaMalloc((void**)&c->d_box_index, S.box_index.size() * sizeof(int)));
   if (e == cudaSuccess) ok(cudaMemcpy(c->d_box_index, S.box_index.data(), S.box_index.size() * sizeof(int), cudaMemcpyHostToDevice));
-  std::vector<double> kpg((size_t)S.Nk * S.npw_max * 3, 0.0);
-  for (int k = 0; k < S.Nk; ++k)
+  std::vector<double> kpg((size_t)S.Nkt * S.npw_max * 3, 0.0);
+  for (int k = 0; k < S.Nkt; ++k)
     for (int g = 0; g < S.npw[k]; ++g)
       for (int d = 0; d < 3; ++d) {
         const auto& m = S.miller[k][g];
@@ -457,8 +474,21 @@ int init_context(const tc_params* params, bool own_workspace, tc_ctx** out, std:
   c->d_hartV = up(S.hartV);
   c->d_hartU = up(S.hartU);
   c->d_hartUs = up(S.hartUs);
-  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_occ, nj * sizeof(double)));
-  if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_occ, nj * sizeof(double)));
+  // occupations of the mesh points, then (band contexts) of the band points
+  const size_t nj_all = (size_t)S.Nkt * S.nb;
+  if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_occ, nj_all * sizeof(double)));
+  if (e == cudaSuccess) ok(cudaMallocHost((void**)&c->h_occ, nj_all * sizeof(double)));
+  if (S.nkb > 0) {
+    std::vector<double> band((size_t)S.nkb * 4);
+    for (int b = 0; b < S.nkb; ++b) {
+      for (int d = 0; d < 3; ++d) band[4 * b + d] = S.Wb[b][d];
+      band[4 * b + 3] = S.gamma_b[b];
+    }
+    if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_band, band.size() * sizeof(double)));
+    if (e == cudaSuccess) ok(cudaMemcpy(c->d_band, band.data(), band.size() * sizeof(double), cudaMemcpyHostToDevice));
+    const size_t nbs = (size_t)2 * S.nkb * S.no * S.nb * tc::kBandScalars;
+    if (e == cudaSuccess) ok(cudaMalloc((void**)&c->d_bs, nbs * sizeof(double2)));
+  }
   // workspace: real-space fields, per-side fields, correction scalars, scratch (zeroed once)
   if (own_workspace) {
     const WsLayout L = ws_layout(c);
@@ -534,6 +564,26 @@ int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st) {
   return TC_OK;
 }
 
+// Band contexts: mesh occupations [Nk][nb] then band-point occupations [nkb][nb] into c->d_occ.
+int stage_occ_band(tc_ctx* c, const double* occ, const double* band_occ, cudaStream_t st) {
+  const size_t nm = (size_t)c->S.Nk * c->S.nb, nbnd = (size_t)c->S.nkb * c->S.nb;
+  for (size_t i = 0; i < nm; ++i)
+    if (!(occ[i] >= 0.0 && occ[i] <= 1.0)) return ::fail(c, TC_ERR_ARG, "occupations must lie in [0, 1]");
+  for (size_t i = 0; i < nbnd; ++i)
+    if (!(band_occ[i] >= 0.0 && band_occ[i] <= 1.0)) return ::fail(c, TC_ERR_ARG, "band occupations must lie in [0, 1]");
+  if (c->occ_pending) {
+    const cudaError_t w = cudaEventSynchronize(c->occ_ev);
+    if (w != cudaSuccess) return cuda_fail(c, w, "occupation upload wait");
+  }
+  std::memcpy(c->h_occ, occ, nm * sizeof(double));
+  std::memcpy(c->h_occ + nm, band_occ, nbnd * sizeof(double));
+  cudaError_t e = cudaMemcpyAsync(c->d_occ, c->h_occ, (nm + nbnd) * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && c->occ_ev) e = cudaEventRecord(c->occ_ev, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "occ upload");
+  c->occ_pending = c->occ_ev != nullptr;
+  return TC_OK;
+}
+
 int launch_biortho(tc_ctx* c, double2* phi, double2* chi, int* status, cudaStream_t st) {
   const Setup& S = c->S;
   const size_t smem = (size_t)S.nb * 2 * S.nb * sizeof(double2);
@@ -573,7 +623,7 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
 tc_status tc_layout(const tc_ctx* c, int* nk, int* npw_max, const int** npw_per_k, const int** miller) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return TC_ERR_STATE;
-  if (nk) *nk = c->S.Nk;
+  if (nk) *nk = c->S.Nkt;   // band contexts: the mesh points, then the band points
   if (npw_max) *npw_max = c->S.npw_max;
   if (npw_per_k) *npw_per_k = c->npw_host.data();
   if (miller) *miller = c->S.miller_flat.data();
@@ -666,6 +716,7 @@ tc_status tc_apply(tc_ctx* c, const void* phi, const void* chi, const double* oc
                    void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
+  if (c->S.nkb > 0) return fail(c, TC_ERR_STATE, "band context: use tc_apply_band");
   if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
   if (!outR && !outL) return TC_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -681,10 +732,47 @@ tc_status tc_apply(tc_ctx* c, const void* phi, const void* chi, const double* oc
   return TC_OK;
 }
 
+tc_status tc_init_band(const tc_params* params, int nkb, const double* kfrac_band, tc_ctx** out) {
+  if (!params || !out || !kfrac_band || nkb < 1) {
+    g_init_err = "tc_init_band: null pointer or nkb < 1";
+    return TC_ERR_ARG;
+  }
+  std::string err;
+  const int r = tc::init_context(params, true, out, err, nkb, kfrac_band);
+  g_init_err = err;
+  return (tc_status)r;
+}
+
+tc_status tc_apply_band(tc_ctx* c, const void* phi, const void* chi, const double* occ, const void* band_phi,
+                        const void* band_chi, const double* band_occ, void* outR, void* outL, void* stream) {
+  if (!c) return TC_ERR_STATE;
+  if (c->S.nkb == 0) return fail(c, TC_ERR_STATE, "not a band context (tc_init_band)");
+  if (!phi || !chi || !occ || !band_phi || !band_chi || !band_occ) return fail(c, TC_ERR_ARG, "null input pointer");
+  if (!outR && !outL) return TC_OK;
+  for (const void* p : {phi, chi, band_phi, band_chi, (const void*)outR, (const void*)outL})
+    if (p && !is_device_ptr(p)) return fail(c, TC_ERR_ARG, "band launches take device pointers only");
+  if (const int f = tc::injected_fault("launch")) return fail(c, (tc_status)f, "injected fault (TC_FAULT): no device work done");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ro = tc::stage_occ_band(c, occ, band_occ, st);
+  if (ro != TC_OK) return (tc_status)ro;
+  double tw[NT];
+  term_weights(c, tw, 1.0, 1.0);
+  const double2* a = static_cast<const double2*>(phi);
+  const double2* b = static_cast<const double2*>(chi);
+  const double2* ba = static_cast<const double2*>(band_phi);
+  const double2* bb = static_cast<const double2*>(band_chi);
+  double2* oR = static_cast<double2*>(outR);
+  double2* oL = static_cast<double2*>(outL);
+  const int r = c->prec == TC_FP64 ? dispatch_run_band<double>(c, a, b, ba, bb, oR, oL, tw, st)
+                                   : dispatch_run_band<float>(c, a, b, ba, bb, oR, oL, tw, st);
+  return (tc_status)r;
+}
+
 tc_status tc_energy(tc_ctx* c, const void* phi, const void* chi, const double* occ, double* E_total,
                     double* E_terms, void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
+  if (c->S.nkb > 0) return fail(c, TC_ERR_STATE, "band context: use tc_apply_band");
   if (!phi || !chi || !occ || !E_total) return fail(c, TC_ERR_ARG, "null pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const tc::Setup& S = c->S;
@@ -730,6 +818,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
                          void* dE_dphiL, double* dE_dA, double* dE_dC, void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
+  if (c->S.nkb > 0) return fail(c, TC_ERR_STATE, "band context: use tc_apply_band");
   if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tc::Setup& S = c->S;
@@ -837,6 +926,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
 tc_status tc_biorthonormalize(tc_ctx* c, void* phi, void* chi, void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return fail(c, TC_ERR_STATE, "batch context: use tc_apply_batch or tc_batch_cell");
+  if (c->S.nkb > 0) return fail(c, TC_ERR_STATE, "band context: use tc_apply_band");
   if (!phi || !chi) return fail(c, TC_ERR_ARG, "null orbital pointer");
   const tc::Setup& S = c->S;
   if (S.nb > kBiorthoMaxBands) return fail(c, TC_ERR_UNSUPPORTED, "tc_biorthonormalize supports at most 64 bands");
@@ -966,6 +1056,7 @@ tc_status tc_autotune(tc_ctx* c, const void* phi, const void* chi, const double*
                       void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch || !c->ws_owned) return fail(c, TC_ERR_STATE, "autotuning needs a single-cell context from tc_init");
+  if (c->S.nkb > 0) return fail(c, TC_ERR_STATE, "band context: use tc_apply_band");
   if (!phi || !chi || !occ) return fail(c, TC_ERR_ARG, "null input pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const tc::Setup& S = c->S;

@@ -24,9 +24,9 @@ struct tc_ctx {
   std::string err;
   int device = 0;
   // basis
-  int* d_box_index = nullptr;      // [Nk][npw_max]
-  double* d_kpg = nullptr;         // [Nk][npw_max][3]
-  int* d_delta_id = nullptr;       // [Nk][Nk]
+  int* d_box_index = nullptr;      // [Nkt][npw_max] (mesh and band points)
+  double* d_kpg = nullptr;         // [Nkt][npw_max][3]
+  int* d_delta_id = nullptr;       // [Nkt][Nkt]
   void* d_delta = nullptr;         // [ndelta][3] T
   void* d_tabV = nullptr;          // [ndelta][2][N] T
   void* d_tabU = nullptr;          // [ndelta][2][N] T
@@ -77,6 +77,13 @@ struct tc_ctx {
   // box indices per axis that a pair-density spectrum can occupy (tc::pair_support_len); the pair
   // chains use their pruned transforms when it fits the compiled support length (large: never)
   int pair_support = 1 << 30;
+  // output orbitals of an apply: Nk nb at the mesh points, or nkb nb at the band points of a band
+  // context (tc_init_band); band h3 chunks; band constants [nkb][4] = (W, Gamma_b) and the band
+  // correction scalars [2][nkb][nocc][nbands][kBandScalars] (device)
+  int nj_out = 0;
+  int so_band = 1;
+  double* d_band = nullptr;
+  double2* d_bs = nullptr;
   // when set for one launch: a context with the same partners (occupied bands, occupations, cell,
   // precision) whose last launch left its partner-only fields (densities, Hartree-type fields,
   // occupied-pair stage) for the same sides; they are copied instead of recomputed
@@ -97,13 +104,18 @@ namespace tc {
 // Context construction without the public wrapper: all tables, staging buffers
 // and -- if own_workspace -- the workspace block.  Returns a tc_status; on
 // failure *out is null and err holds the reason.
-int init_context(const tc_params* p, bool own_workspace, tc_ctx** out, std::string& err);
+int init_context(const tc_params* p, bool own_workspace, tc_ctx** out, std::string& err, int nkb = 0,
+                 const double* kfrac_band = nullptr);
+// Complex FP64 scalars per (side, band point, occupied m, output j) of the band corrections:
+// 0 <bra_m|ket_j>, 1-3 <bra_m|grad ket_j>, 4 <bra_m|(W.h1) ket_j>, 5-6 mean(bra_m^* ket_j V2_s),
+// 7-9 mean(ket_j h3b(m)), 10-12 <bra_m|w_j> (w_j including its correction).
+constexpr int kBandScalars = 13;
 void destroy_context(tc_ctx* c);
 WsLayout ws_layout(const tc_ctx* c);
 // Chooses the partner-chunk counts of c for the current device (needs c->S).
 void choose_splits(tc_ctx* c);
 // n^3 volumes of one side's field block (see fill_side).
-size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max);
+size_t side_field_vols(int Nk, int nb, int no, int so_max, int sc_max, int nj_out, int nkb, int so_band);
 void ws_assign(tc_ctx* c, char* base, const WsLayout& L);
 // Both operator sides into outR / outL (device pointers) on st, all terms of term_mask.
 int apply_device(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, cudaStream_t st);
@@ -115,6 +127,8 @@ void free_symmetry(tc_ctx* c);
 int launch_sym_unfold(tc_ctx* c, double2* a, double2* b, cudaStream_t st);
 // Validates occ (Nk*nb values in [0, 1]) and enqueues its upload into c->d_occ on st.
 int stage_occ(tc_ctx* c, const double* occ, cudaStream_t st);
+// Band contexts: mesh occupations, then those of the band points.
+int stage_occ_band(tc_ctx* c, const double* occ, const double* band_occ, cudaStream_t st);
 // Operator on nsides sides (1: right only into outR; 2: both) for orbitals already on the device.
 int apply_sides(tc_ctx* c, const double2* phi, const double2* chi, double2* outR, double2* outL, int nsides,
                 cudaStream_t st);
@@ -135,7 +149,8 @@ void set_thread_error(const std::string& msg);
 // nsides: 2 (right and left) or 1 (right only).
 template <typename T, int N>
 int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2* outR, double2* outL,
-                 const double* tw, int nsides, cudaStream_t st);
+                 const double* tw, int nsides, cudaStream_t st, const double2* bphi = nullptr,
+                 const double2* bchi = nullptr);
 template <typename T, int N> int prepare_kernels(tc_ctx* ctx);
 template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cudaStream_t st);
 template <typename T, int N> size_t scratch_needed(const Setup& S, int so_max, int sc_max);

@@ -667,6 +667,7 @@ tc_status tc_davidson_step(tc_ctx* c, const void* phi, const void* chi, const do
                            void* chi_out, void* eig_out, int* dim_out, void* stream) {
   if (!c) return TC_ERR_STATE;
   if (c->batch) return dav_fail(c, TC_ERR_STATE, "batch context: use a single-cell context");
+  if (c->S.nkb > 0) return dav_fail(c, TC_ERR_STATE, "band context: use a context from tc_init");
   if (!phi || !chi || !occ || !phi_out || !chi_out) return dav_fail(c, TC_ERR_ARG, "null pointer");
   if (phi_out == phi || phi_out == chi || chi_out == phi || chi_out == chi || phi_out == chi_out)
     return dav_fail(c, TC_ERR_ARG, "output arrays must not alias the inputs or each other");

@@ -37,7 +37,10 @@ template <typename T> struct SideArgs {
   cplx<T>* w;            // [sc][Nk][nb][3][N]
   cplx<T>* Z;            // [Nk][no][3][N]  -(s2b tw2bx1 grad ket_q + tw3a4 h3a4(q))
   cplx<T>* Y;            // [Nk][nb][3][N]  tw3b3 h1 ket_j - s2b tw2bx2 grad ket_j
-  double* cs;            // [Nk*nb][no][6]: O_qj, X_pp, X_ap (re, im each): 3b6 correction scalars
+  double* cs;            // [nj_out][no][6]: O_qj, X_pp, X_ap (re, im each): 3b6 correction scalars
+  cplx<T>* v2;           // [nkb][4]  band points: V2_pp, V2_ap, V3_pp, V3_ap (see tc_band.cuh)
+  cplx<T>* bh3a;         // [so][nkb no][3][N]  band points: h3 (3a4 kind) of their occupied orbitals
+  cplx<T>* bh3b;         // [so][nkb no][3][N]  band points: h3 (3b kind)
   const T* tabV;         // [ndelta][2][N] -> this side's V at offset side*N
   T s2b;                 // +1 right, -1 left (sign of the grad u . grad terms)
   int side;
@@ -70,6 +73,16 @@ template <typename T> struct Params {
   const T* symcart;      // [nops][9] Cartesian S^dagger = S_c^T, row-major
   const int* star_off;   // [nirr + 1] offsets into star_k
   const int* star_k;     // [Nk] k-points grouped by their irreducible point
+  // launch ranges (a mesh apply: kstride = Nk, j0 = 0, nj_out = Nk nb, i2_0 = 0, nq2 = Nk no)
+  int kstride;           // row stride of delta_id: k-points with orbitals (mesh + band points)
+  int j0, nj_out;        // output orbitals j0 .. j0 + nj_out - 1 (pair chains, 3b4, finalize, Y);
+                         // acc, w, Y and cs are indexed by j - j0
+  int i2_0, nq2;         // occupied-pair stage: q2 items i2_0 .. i2_0 + nq2 - 1 (item = k no + mu)
+  int h3_only;           // occupied-pair stage: the two h3 kinds only (parallel spins, no h6)
+  int band;              // outputs at band points: no SCF-mesh 3b6 corrections in k_finalize
+  int nkb;               // band points (band contexts)
+  const double* bandc;   // [nkb][4]: W (3), Gamma_b
+  double2* bs;           // [2][nkb][no][nb][13] band correction scalars (tc_band.cuh)
   SideArgs<T> side[2];
 };
 

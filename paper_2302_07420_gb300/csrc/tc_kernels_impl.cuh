@@ -122,11 +122,12 @@ __global__ void __launch_bounds__(Cfg<N>::threads) k_fft3d(cplx<T>* data, cplx<T
 }
 
 // ---------------------------------------------------------------------------
-// Orbitals to real space: grid (Nk*nb, 4 components, 2 sets).  Component 0 is
+// Orbitals to real space: grid (orbitals, 4 components, 2 sets).  Component 0 is
 // psi = FT^{-1}[c], components 1..3 are d_d psi = FT^{-1}[i (k+G)_d c].
 template <typename T, int N>
 __global__ void __launch_bounds__(Cfg<N>::threads)
-    k_orbitals(const double2* __restrict__ cphi, const double2* __restrict__ cchi, const int* __restrict__ box_index,
+    k_orbitals(const double2* __restrict__ cphi, const double2* __restrict__ cchi, const double2* __restrict__ bphi,
+               const double2* __restrict__ bchi, int nj_mesh, const int* __restrict__ box_index,
                const double* __restrict__ kpg, int npw_max, int nb, cplx<T>* phi, cplx<T>* chi, cplx<T>* gphi,
                cplx<T>* gchi, cplx<T>* gwork) {
   using G = Geo<N>;
@@ -134,7 +135,9 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
   cplx<T>* V = work_vol<T, N>(smraw, gwork);
   const int j = blockIdx.x, comp = blockIdx.y, set = blockIdx.z;
   const int k = j / nb;
-  const double2* c = (set == 0 ? cphi : cchi) + (size_t)j * npw_max;
+  // orbitals j >= nj_mesh are those of band points (their own input arrays)
+  const double2* c = j < nj_mesh ? (set == 0 ? cphi : cchi) + (size_t)j * npw_max
+                                 : (set == 0 ? bphi : bchi) + (size_t)(j - nj_mesh) * npw_max;
   for (int i = threadIdx.x; i < G::vol; i += blockDim.x) V[i] = cplx<T>{0, 0};
   __syncthreads();
   for (int g = threadIdx.x; g < npw_max; g += blockDim.x) {
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   const int M = P.Nk * P.no;                                   // occupied states
   // with crystal symmetry only the q2 of irreducible k-points have CTAs (the rest are unfolded)
   const int item = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
-  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : item;
+  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : P.i2_0 + item;
   const int k2 = i2 / P.no, mu2 = i2 % P.no;
   const int q2 = k2 * P.nb + mu2;
   const int i1_begin = (int)((long long)chunk * M / P.so), i1_end = (int)((long long)(chunk + 1) * M / P.so);
@@ -296,8 +299,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   cplx<T>* FAB = vol_slot<T, N>(P, sm, 5, NS, true);
   const size_t NN = G::nn;
   const T f2 = (T)(P.occ[q2] / P.Nk);
-  cplx<T>* h3a4 = S.h3a4 + ((size_t)chunk * M + i2) * 3 * NN;
-  cplx<T>* h3b = S.h3b + ((size_t)chunk * M + i2) * 3 * NN;
+  cplx<T>* h3a4 = S.h3a4 + ((size_t)chunk * P.nq2 + (i2 - P.i2_0)) * 3 * NN;
+  cplx<T>* h3b = S.h3b + ((size_t)chunk * P.nq2 + (i2 - P.i2_0)) * 3 * NN;
   const cplx<T>* bra2 = S.bra + (size_t)q2 * NN;
   const cplx<T>* ket2 = S.ket + (size_t)q2 * NN;
   for (int r = threadIdx.x; r < G::vol; r += blockDim.x) FAB[r] = cplx<T>{0, 0};   // padded layout
@@ -312,8 +315,8 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
   __syncthreads();
   for (int i1 = i1_begin; i1 < i1_end; ++i1) {
     const int k1 = i1 / P.no, mu1 = i1 % P.no;
-    const int id12 = P.delta_id[k2 * P.Nk + k1];   // Delta = k2 - k1 -> for P(q1,q2)
-    const int id21 = P.delta_id[k1 * P.Nk + k2];   // Delta = k1 - k2 -> for P(q2,q1)
+    const int id12 = P.delta_id[k2 * P.kstride + k1];   // Delta = k2 - k1 -> for P(q1,q2)
+    const int id21 = P.delta_id[k1 * P.kstride + k2];   // Delta = k1 - k2 -> for P(q2,q1)
     const T* d12 = P.delta + id12 * 3;
     const T* d21 = P.delta + id21 * 3;
     {
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
       const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
       const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
       for (int sp = 0; sp < 2; ++sp) {
-        if (sp == 1 && !ap_here) continue;
+        if (sp == 1 && (!ap_here || P.h3_only)) continue;
         const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
         for (int d = 0; d < 3; ++d) {
           const PComp<T> q21 = pcomp_setup<T>(P, d21, d), q12 = pcomp_setup<T>(P, d12, d);
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
     }
   }
   // 3a2 corrections of this q2: (f2/Nk)/Omega^2 sum_s [c_s F0 + (4 pi A_s/Nk) FT^{-1}[u~_s F_ab]]
-  if (P.div && f2 != T(0)) {
+  if (P.div && f2 != T(0) && !P.h3_only) {
     const T pref = (T)(f2 * P.invOm2);
     const T c0 = (T)(P.corr_c[0] + P.corr_c[1]);
     const cplx<T> cF0 = {(T)(c0 * sF0[0]), (T)(c0 * sF0[1])};
@@ -536,7 +539,7 @@ template <typename T, int N> __global__ void k_unfold(Params<T> P) {
 template <typename T, int N> __global__ void k_sum_parts(Params<T> P, int which) {
   const SideArgs<T>& S = P.side[blockIdx.y];
   const size_t NN = (size_t)N * N * N;
-  const size_t nj = (size_t)P.Nk * P.nb, M = (size_t)P.Nk * P.no;
+  const size_t nj = (size_t)P.nj_out, M = (size_t)P.nq2;
   const int nparts = which == 0 ? P.so : P.sc;
   cplx<T>* a = which == 0 ? S.h3a4 : S.acc;
   cplx<T>* b = which == 0 ? S.h3b : S.w;
@@ -571,7 +574,7 @@ template <typename T, int N> __global__ void k_vloc(Params<T> P) {
 template <typename T, int N> __global__ void k_prep_zy(Params<T> P) {
   const SideArgs<T>& S = P.side[blockIdx.y];
   const size_t NN = (size_t)N * N * N;
-  const size_t nz = (size_t)P.Nk * P.no * 3, ny = (size_t)P.Nk * P.nb * 3;
+  const size_t nz = (size_t)P.Nk * P.no * 3, ny = (size_t)P.nj_out * 3;
   const T* tw = P.tw;
   const T zg = -S.s2b * tw[T2BX1], zh = -tw[T3A4], y1 = tw[T3B3], yg = -S.s2b * tw[T2BX2];
   const size_t total = (nz + ny) * NN;
@@ -583,7 +586,7 @@ template <typename T, int N> __global__ void k_prep_zy(Params<T> P) {
       const size_t q = (qo / P.no) * P.nb + qo % P.no;
       S.Z[e] = zg * S.gket[(q * 3 + d) * NN + r] + zh * S.h3a4[e];
     } else {
-      const size_t jd = v - nz, d = jd % 3, j = jd / 3;
+      const size_t jd = v - nz, d = jd % 3, j = P.j0 + jd / 3;   // Y is indexed by j - j0
       S.Y[jd * NN + r] = y1 * (S.h1[d * NN + r] * S.ket[j * NN + r]) + yg * S.gket[(j * 3 + d) * NN + r];
     }
   }
@@ -615,17 +618,17 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
   const SideArgs<T>& S = P.side[blockIdx.y];
   // with crystal symmetry only orbitals of irreducible k-points are computed (the rest are unfolded)
   const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
-  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
-  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int jo = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, j = P.j0 + jo, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.nj_out;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
   cplx<T>* C = vol_slot<T, N>(P, sm, 1, NS);
   cplx<T>* A = vol_slot<T, N>(P, sm, 2, NS);
   const size_t NN = G::nn;
   const cplx<T>* ketj = S.ket + (size_t)j * NN;
-  const cplx<T>* Yj = S.Y + (size_t)j * 3 * NN;
-  cplx<T>* acc = S.acc + ((size_t)chunk * nj + j) * NN;
-  cplx<T>* w = S.w + ((size_t)chunk * nj + j) * 3 * NN;
+  const cplx<T>* Yj = S.Y + (size_t)jo * 3 * NN;
+  cplx<T>* acc = S.acc + ((size_t)chunk * nj + jo) * NN;
+  cplx<T>* w = S.w + ((size_t)chunk * nj + jo) * 3 * NN;
   const T* tw = P.tw;
   const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
   const bool need_z = tw[T2BX1] != T(0) || tw[T3A4] != T(0);
@@ -641,7 +644,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
   __syncthreads();
   for (int qi = qi_begin; qi < qi_end; ++qi) {
     const int kq = qi / P.no, mu = qi % P.no;
-    const int did = P.delta_id[kj * P.Nk + kq];
+    const int did = P.delta_id[kj * P.kstride + kq];
     const T* dl = P.delta + did * 3;
     const T* Vt = S.tabV + ((size_t)did * 2 + S.side) * NN;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
@@ -672,7 +675,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
           const T sr = block_sum<T>(xr, red);
           const T si = block_sum<T>(xi, red);
           if (threadIdx.x == 0) {
-            double* cs = S.cs + ((size_t)j * P.no + mu) * 6;
+            double* cs = S.cs + ((size_t)jo * P.no + mu) * 6;
             cs[2 + 2 * s] = sr;
             cs[3 + 2 * s] = si;
             if (s == 0) { cs[0] = A[0].x; cs[1] = A[0].y; }
@@ -792,15 +795,15 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
   const SideArgs<T>& S = P.side[blockIdx.y];
   // with crystal symmetry only orbitals of irreducible k-points are computed (the rest are unfolded)
   const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
-  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
-  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int jo = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, j = P.j0 + jo, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.nj_out;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = vol_slot<T, N>(P, sm, 0, NS);
   cplx<T>* A = vol_slot<T, N>(P, sm, 1, NS);
   const size_t NN = G::nn;
   // chunk 0 adds to the complete accumulator (part 0); the others to their own zeroed parts
-  cplx<T>* acc = S.acc + ((size_t)chunk * nj + j) * NN;
-  const cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  cplx<T>* acc = S.acc + ((size_t)chunk * nj + jo) * NN;
+  const cplx<T>* w = S.w + (size_t)jo * 3 * NN;
   const T t3b4 = P.tw[T3B4];
   if (t3b4 == T(0)) return;
   if (chunk > 0) {
@@ -809,7 +812,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_3b4(Params<T> P) {
   }
   for (int qi = qi_begin; qi < qi_end; ++qi) {
     const int kq = qi / P.no, mu = qi % P.no;
-    const int did = P.delta_id[kj * P.Nk + kq];
+    const int did = P.delta_id[kj * P.kstride + kq];
     const T* dl = P.delta + did * 3;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
     {
@@ -856,14 +859,15 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
   const SideArgs<T>& S = P.side[side];
   double2* out = side == 0 ? outR : outL;
   if (out == nullptr) return;
-  const int j = P.sym ? P.irr[blockIdx.x / P.nb] * P.nb + blockIdx.x % P.nb : blockIdx.x, kj = j / P.nb;
+  const int jo = P.sym ? P.irr[blockIdx.x / P.nb] * P.nb + blockIdx.x % P.nb : blockIdx.x;
+  const int j = P.j0 + jo, kj = j / P.nb;
   const size_t NN = G::nn;
   const cplx<T>* ketj = S.ket + (size_t)j * NN;
   const cplx<T>* gketj = S.gket + (size_t)j * 3 * NN;
-  const cplx<T>* acc = S.acc + (size_t)j * NN;
-  const cplx<T>* w = S.w + (size_t)j * 3 * NN;
+  const cplx<T>* acc = S.acc + (size_t)jo * NN;
+  const cplx<T>* w = S.w + (size_t)jo * 3 * NN;
   const T t2bh1 = P.tw[T2BH1] * S.s2b, t3a3 = P.tw[T3A3];
-  const bool corr = P.div && P.tw[T3B6] != T(0);
+  const bool corr = P.div && P.tw[T3B6] != T(0) && !P.band;
   const T a0 = (T)(4.0 * 3.14159265358979323846 * P.A[0] / P.Nk), a1 = (T)(4.0 * 3.14159265358979323846 * P.A[1] / P.Nk);
   const double n0x = corr ? (double)S.nt[0].x : 0.0, n0y = corr ? (double)S.nt[0].y : 0.0;
   fwd3d<T, N>(
@@ -884,7 +888,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
             const int q = kj * P.nb + mu;
             const double fq = P.occ[q];
             if (fq == 0.0) continue;
-            const double* cs = S.cs + ((size_t)j * P.no + mu) * 6;
+            const double* cs = S.cs + ((size_t)jo * P.no + mu) * 6;
             const cplx<T> O = {(T)cs[0], (T)cs[1]};
             const cplx<T> X0 = {(T)cs[2], (T)cs[3]}, X1 = {(T)cs[4], (T)cs[5]};
             const double cc = P.corr_c[0] + P.corr_c[1];
@@ -898,7 +902,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads)
       },
       [&](int a, int b, int c, cplx<T> v) { V[G::sidx(a, b, c)] = P.invN * v; });
   __syncthreads();
-  double2* o = out + (size_t)j * P.npw_max;
+  double2* o = out + (size_t)jo * P.npw_max;
   for (int g = threadIdx.x; g < P.npw_max; g += blockDim.x) {
     const int bi = box_index[(size_t)kj * P.npw_max + g];
     if (bi < 0) {

@@ -154,6 +154,7 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(TC_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   c.device = dev;
+  c.nj_out = S.Nk * S.nb;
   {
     // the same grid rules as tc_init: derived left occupied-pair fields, pruned pair chains
     const int span = tc::miller_span(S.miller);

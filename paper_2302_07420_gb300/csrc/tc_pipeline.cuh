@@ -7,6 +7,7 @@
 #include "tc_ctx.hpp"
 #include "tc_kernels_impl.cuh"
 #include "tc_pruned.cuh"
+#include "tc_band.cuh"
 
 namespace tc {
 
@@ -23,11 +24,14 @@ template <typename T, int N> static void fill_side(tc_ctx* ctx, int side, SideAr
   s.h6 = take(1); s.vloc = take(1);
   s.h3a4 = take((size_t)ctx->so_max * S.Nk * S.no * 3);
   s.h3b = take((size_t)ctx->so_max * S.Nk * S.no * 3);
-  s.acc = take((size_t)ctx->sc_max * S.Nk * S.nb);
-  s.w = take((size_t)ctx->sc_max * S.Nk * S.nb * 3);
+  s.acc = take((size_t)ctx->sc_max * ctx->nj_out);
+  s.w = take((size_t)ctx->sc_max * ctx->nj_out * 3);
   s.Z = take((size_t)S.Nk * S.no * 3);
-  s.Y = take((size_t)S.Nk * S.nb * 3);
-  s.cs = ctx->d_cs + (size_t)side * S.Nk * S.nb * S.no * 6;
+  s.Y = take((size_t)ctx->nj_out * 3);
+  s.v2 = take((size_t)S.nkb * 4);
+  s.bh3a = take((size_t)ctx->so_band * S.nkb * S.no * 3);
+  s.bh3b = take((size_t)ctx->so_band * S.nkb * S.no * 3);
+  s.cs = ctx->d_cs + (size_t)side * ctx->nj_out * S.no * 6;
   const cplx<T>* phi = reinterpret_cast<const cplx<T>*>(ctx->d_phi);
   const cplx<T>* chi = reinterpret_cast<const cplx<T>*>(ctx->d_chi);
   const cplx<T>* gphi = reinterpret_cast<const cplx<T>*>(ctx->d_gphi);
@@ -70,6 +74,16 @@ template <typename T, int N> static Params<T> make_params(tc_ctx* ctx, const dou
   else P.symcart = reinterpret_cast<const T*>(ctx->d_symcart32);
   P.star_off = ctx->d_star_off;
   P.star_k = ctx->d_star_k;
+  P.kstride = S.Nkt;
+  P.j0 = 0;
+  P.nj_out = S.Nk * S.nb;
+  P.i2_0 = 0;
+  P.nq2 = S.Nk * S.no;
+  P.h3_only = 0;
+  P.band = 0;
+  P.nkb = S.nkb;
+  P.bandc = ctx->d_band;
+  P.bs = ctx->d_bs;
   fill_side<T, N>(ctx, 0, P.side[0]);
   fill_side<T, N>(ctx, 1, P.side[1]);
   return P;
@@ -117,6 +131,7 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
   TC_SET_SMEM((k_spec_fwd<T, N>), vb1);
   TC_SET_SMEM((k_hartree_inv<T, N>), vb1);
   TC_SET_SMEM((k_finalize<T, N>), vb1);
+  TC_SET_SMEM((k_band_v2<T, N>), vb1);
   TC_SET_SMEM((k_occ_pairs<T, N>), (smem_vols<T, N>(4) * vb));
   TC_SET_SMEM((k_pair_chain<T, N>), (smem_vols<T, N>(3) * vb));
   TC_SET_SMEM((k_pair_3b4<T, N>), (smem_vols<T, N>(2) * vb));
@@ -136,9 +151,10 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
 // (at most 8 per orbital in k_orbitals).  The uses never overlap in time.
 template <typename T, int N> size_t scratch_needed(const Setup& S, int so_max, int sc_max) {
   const size_t vb = (size_t)vol_bytes<T, N>();
-  const size_t a = (size_t)2 * S.Nk * S.no * so_max * 6 * vb;
-  const size_t b = (size_t)2 * S.Nk * S.nb * sc_max * 3 * vb;
-  const size_t c = Fit<T, N>::one ? 0 : (size_t)8 * S.Nk * S.nb * vb;
+  // (band contexts: the band points' occupied-pair launch, at most 8 chunks)
+  const size_t a = (size_t)2 * std::max(S.Nk * so_max, S.nkb * 8) * S.no * 6 * vb;
+  const size_t b = (size_t)2 * std::max(S.Nk, S.nkb) * S.nb * sc_max * 3 * vb;
+  const size_t c = Fit<T, N>::one ? 0 : (size_t)8 * S.Nkt * S.nb * vb;
   return std::max(a, std::max(b, c));
 }
 
@@ -171,9 +187,11 @@ static inline int stage_collect(tc_ctx* ctx, int nstages, const int* launches) {
   return TC_OK;
 }
 
+// Band contexts (S.nkb > 0): bphi / bchi are the band points' orbitals and the outputs are theirs
+// (tc_band.cuh); every partner-only stage is the mesh one.
 template <typename T, int N>
 int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2* outR, double2* outL,
-                 const double* tw, int nsides, cudaStream_t st) {
+                 const double* tw, int nsides, cudaStream_t st, const double2* bphi, const double2* bchi) {
   const auto& S = ctx->S;
   const int TH = Cfg<N>::threads;
   const int vb = vol_bytes<T, N>();
@@ -181,7 +199,20 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   Params<T> P = make_params<T, N>(ctx, tw);
   P.so = ctx->split_occ[nsides - 1];
   P.sc = ctx->split_chain[nsides - 1];
-  const int nj = S.Nk * S.nb;
+  const bool band = S.nkb > 0;
+  if (band && (nsides != 2 || !bphi || !bchi || P.sym || ctx->partners_from)) {
+    ctx->err = "band context: two-sided launches with band-point orbitals only";
+    return TC_ERR_STATE;
+  }
+  const int nj = S.Nk * S.nb;                       // mesh orbitals (partners)
+  const int nj_all = S.Nkt * S.nb;                  // orbitals to real space
+  if (band) {
+    P.band = 1;
+    P.j0 = nj;
+    P.nj_out = S.nkb * S.nb;
+  }
+  // band points: every divergence correction (all need div_correction) and the fields they take
+  const bool band_corr = band && P.div;
   const int pw_blocks = 2 * 152;
   int nl[6] = {1, 9, 0, 1, 1, 1};   // kernel launches per stage
   // pair densities whose spectra fit the compiled support take the pruned transforms
@@ -189,13 +220,14 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   const bool pruned = LP < N && ctx->pair_support <= LP;
   // 1. orbitals to real space
   stage_mark(ctx, st, 0);
-  k_orbitals<T, N><<<dim3(nj, 4, 2), TH, vb1, st>>>(cphi, cchi, ctx->d_box_index, ctx->d_kpg, S.npw_max, S.nb,
+  k_orbitals<T, N><<<dim3(nj_all, 4, 2), TH, vb1, st>>>(cphi, cchi, bphi, bchi, nj, ctx->d_box_index, ctx->d_kpg,
+                                                   S.npw_max, S.nb,
                                                    (cplx<T>*)ctx->d_phi, (cplx<T>*)ctx->d_chi,
                                                    (cplx<T>*)ctx->d_gphi, (cplx<T>*)ctx->d_gchi,
                                                    (cplx<T>*)ctx->d_scratch);
   TC_CHECK_LAUNCH("k_orbitals");
   if (sizeof(T) == 4 && S.prm.precision == TC_BF16_STORE) {
-    const size_t no = (size_t)nj * S.N;   // orbitals x box points per set
+    const size_t no = (size_t)nj_all * S.N;   // orbitals x box points per set
     k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_phi, no);
     k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_chi, no);
     k_round_bf16<T><<<2 * pw_blocks, 256, 0, st>>>((cplx<T>*)ctx->d_gphi, 3 * no);
@@ -243,6 +275,11 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   k_spec_fwd<T, N><<<dim3(3, nsides), TH, vb1, st>>>(P, 2);
   k_hartree_inv<T, N><<<dim3(1, nsides), TH, vb1, st>>>(P, 3);
   TC_CHECK_LAUNCH("hartree 3b1");
+  if (band_corr) {
+    k_band_v2<T, N><<<dim3(4 * S.nkb, nsides), TH, vb1, st>>>(P);
+    TC_CHECK_LAUNCH("k_band_v2");
+    nl[1] += 1;
+  }
   // 3. occupied-pair stage
   stage_mark(ctx, st, 2);
   const bool need_a4 = tw[T3A2] != 0 || tw[T3A4] != 0 || tw[T3B2] != 0 || tw[T3B5] != 0;
@@ -286,6 +323,36 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     TC_CHECK_LAUNCH("hartree 3b2");
     nl[2] += 4;
   }
+  if (band_corr) {
+    // occupied-pair fields (both h3 kinds, parallel spins) of the band points' own occupied
+    // orbitals against the mesh partners, both sides, then their q1 -> k_b correction
+    Params<T> Pq = P;
+    Pq.nsmem = smem_vols<T, N>(4);
+    Pq.i2_0 = nj / S.nb * S.no;   // items Nk no ..
+    Pq.nq2 = S.nkb * S.no;
+    Pq.h3_only = 1;
+    Pq.so = ctx->so_band;
+    for (int sd = 0; sd < 2; ++sd) {
+      Pq.side[sd].h3a4 = P.side[sd].bh3a;
+      Pq.side[sd].h3b = P.side[sd].bh3b;
+    }
+    if constexpr (LP < N) {
+      if (pruned)
+        k_occ_pairs_pr<T, N, LP><<<dim3(Pq.nq2 * Pq.so, 2), PrCfg<T, N>::threads, OccSmem<T, N, LP>::bytes, st>>>(Pq);
+    }
+    if (!pruned) k_occ_pairs<T, N><<<dim3(Pq.nq2 * Pq.so, 2), TH, Pq.nsmem * vb, st>>>(Pq);
+    TC_CHECK_LAUNCH("k_occ_pairs (band points)");
+    if (Pq.so > 1) {
+      k_sum_parts<T, N><<<dim3(2 * pw_blocks, 2), 256, 0, st>>>(Pq, 0);
+      TC_CHECK_LAUNCH("k_sum_parts");
+      nl[2] += 1;
+    }
+    k_band_scalars<T, N><<<dim3(S.nkb * S.no * S.nb, 2), 256, 0, st>>>(P, 0);
+    k_band_h3corr<T, N><<<2 * pw_blocks, 256, 0, st>>>(P, 2);
+    k_band_scalars<T, N><<<dim3(S.nkb * S.no * S.nb, 2), 256, 0, st>>>(P, 1);
+    TC_CHECK_LAUNCH("band scalars");
+    nl[2] += 4;
+  }
   k_vloc<T, N><<<dim3(pw_blocks, nsides), 256, 0, st>>>(P);
   TC_CHECK_LAUNCH("k_vloc");
   k_prep_zy<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P);
@@ -294,7 +361,7 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   }
   // 4. pair chains (with symmetry: output orbitals of irreducible k-points only)
   stage_mark(ctx, st, 3);
-  const int nj_items = P.sym ? P.nirr * S.nb : nj;
+  const int nj_items = P.sym ? P.nirr * S.nb : P.nj_out;
   {
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);
@@ -310,6 +377,13 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 1);
       TC_CHECK_LAUNCH("k_sum_parts");
       nl[4] += 1;
+    }
+    if (band_corr) {
+      // w_j + w_c (3a3, 3b4) and its overlaps (3b4)
+      k_band_wc<T, N><<<2 * pw_blocks, 256, 0, st>>>(P, 2);
+      k_band_scalars<T, N><<<dim3(S.nkb * S.no * S.nb, 2), 256, 0, st>>>(P, 2);
+      TC_CHECK_LAUNCH("band w_c");
+      nl[4] += 2;
     }
     Params<T> Pb = P;
     Pb.nsmem = smem_vols<T, N>(2);
@@ -328,6 +402,11 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   }
   // 5. local terms, corrections, back to the sphere
   stage_mark(ctx, st, 5);
+  if (band_corr) {
+    k_band_corr<T, N><<<2 * pw_blocks, 256, 0, st>>>(P, 2);
+    TC_CHECK_LAUNCH("k_band_corr");
+    nl[5] += 1;
+  }
   k_finalize<T, N><<<dim3(nj_items, nsides), TH, vb1, st>>>(P, outR, outL, ctx->d_box_index);
   TC_CHECK_LAUNCH("k_finalize");
   if (P.sym && P.nirr < S.Nk) {
@@ -356,7 +435,7 @@ template <typename T, int N> int run_fft3d(void* data, int batch, int sign, cuda
 
 #define TC_INSTANTIATE(T, N)                                                                             \
   template int run_pipeline<T, N>(tc_ctx*, const double2*, const double2*, double2*, double2*, const double*, \
-                                  int, cudaStream_t);                                                     \
+                                  int, cudaStream_t, const double2*, const double2*);                     \
   template int prepare_kernels<T, N>(tc_ctx*);                                                           \
   template int run_fft3d<T, N>(void*, int, int, cudaStream_t);                                           \
   template size_t scratch_needed<T, N>(const Setup&, int, int);

@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
   __shared__ T red[32];
   const SideArgs<T>& SD = P.side[blockIdx.y];
   const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
-  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
-  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int jo = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, j = P.j0 + jo, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.nj_out;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* A;
@@ -199,9 +199,9 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
   T* tU = SM::tab ? reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) + SM::bB + 2 * SM::bC) : nullptr;
   const size_t NN = G::nn;
   const cplx<T>* ketj = SD.ket + (size_t)j * NN;
-  const cplx<T>* Yj = SD.Y + (size_t)j * 3 * NN;
-  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + j) * NN;
-  cplx<T>* w = SD.w + ((size_t)chunk * nj + j) * 3 * NN;
+  const cplx<T>* Yj = SD.Y + (size_t)jo * 3 * NN;
+  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + jo) * NN;
+  cplx<T>* w = SD.w + ((size_t)chunk * nj + jo) * 3 * NN;
   const T* tw = P.tw;
   const bool need_w = tw[T3A3] != T(0) || tw[T3B4] != T(0);
   const bool need_z = tw[T2BX1] != T(0) || tw[T3A4] != T(0);
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
     const int q = kq * P.nb + mu;
     const T f = (T)(P.occ[q] / P.Nk);
     if (f == T(0)) continue;
-    const int did = P.delta_id[kj * P.Nk + kq];
+    const int did = P.delta_id[kj * P.kstride + kq];
     const T* dl = P.delta + did * 3;
     const T* Vt = SD.tabV + ((size_t)did * 2 + SD.side) * NN;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
         const T sr = block_sum<T>(xr, red);
         const T si = block_sum<T>(xi, red);
         if (threadIdx.x == 0) {
-          double* cs = SD.cs + ((size_t)j * P.no + mu) * 6;
+          double* cs = SD.cs + ((size_t)jo * P.no + mu) * 6;
           cs[2 + 2 * s] = sr;
           cs[3 + 2 * s] = si;
           if (s == 0) { cs[0] = A[0].x; cs[1] = A[0].y; }
@@ -378,8 +378,8 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_3b4_pr(Params<
   extern __shared__ __align__(16) unsigned char smraw[];
   const SideArgs<T>& SD = P.side[blockIdx.y];
   const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
-  const int j = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, kj = j / P.nb;
-  const int M = P.Nk * P.no, nj = P.Nk * P.nb;
+  const int jo = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, j = P.j0 + jo, kj = j / P.nb;
+  const int M = P.Nk * P.no, nj = P.nj_out;
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* A;
@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_3b4_pr(Params<
   }
   T* tU = SM::tab ? reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(smraw) + SM::bB + SM::bC) : nullptr;
   const size_t NN = G::nn;
-  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + j) * NN;
-  const cplx<T>* w = SD.w + (size_t)j * 3 * NN;
+  cplx<T>* acc = SD.acc + ((size_t)chunk * nj + jo) * NN;
+  const cplx<T>* w = SD.w + (size_t)jo * 3 * NN;
   const T t3b4 = P.tw[T3B4];
   if (t3b4 == T(0)) return;
   if (chunk > 0) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_3b4_pr(Params<
     const int q = kq * P.nb + mu;
     const T f = (T)(P.occ[q] / P.Nk);
     if (f == T(0)) continue;
-    const int did = P.delta_id[kj * P.Nk + kq];
+    const int did = P.delta_id[kj * P.kstride + kq];
     const T* dl = P.delta + did * 3;
     const T* Upp = P.tabU + ((size_t)did * 2 + 0) * NN;
     if constexpr (SM::tab) {
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params
   const SideArgs<T>& SD = P.side[blockIdx.y];
   const int M = P.Nk * P.no;
   const int item = blockIdx.x / P.so, chunk = blockIdx.x % P.so;
-  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : item;
+  const int i2 = P.sym ? P.irr[item / P.no] * P.no + item % P.no : P.i2_0 + item;
   const int k2 = i2 / P.no, mu2 = i2 % P.no;
   const int q2 = k2 * P.nb + mu2;
   const int i1_begin = (int)((long long)chunk * M / P.so), i1_end = (int)((long long)(chunk + 1) * M / P.so);
@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params
   cplx<T>* H6 = slice + 4 * (size_t)G::vol;
   const size_t NN = G::nn;
   const T f2 = (T)(P.occ[q2] / P.Nk);
-  cplx<T>* h3a4 = SD.h3a4 + ((size_t)chunk * M + i2) * 3 * NN;
-  cplx<T>* h3b = SD.h3b + ((size_t)chunk * M + i2) * 3 * NN;
+  cplx<T>* h3a4 = SD.h3a4 + ((size_t)chunk * P.nq2 + (i2 - P.i2_0)) * 3 * NN;
+  cplx<T>* h3b = SD.h3b + ((size_t)chunk * P.nq2 + (i2 - P.i2_0)) * 3 * NN;
   const cplx<T>* bra2 = SD.bra + (size_t)q2 * NN;
   const cplx<T>* ket2 = SD.ket + (size_t)q2 * NN;
   for (int r = threadIdx.x; r < S::cvol; r += blockDim.x) FAB[r] = cplx<T>{0, 0};
@@ -520,8 +520,8 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params
     const int q1 = k1 * P.nb + mu1;
     const T f1 = (T)(P.occ[q1] / P.Nk);
     if (f1 == T(0) || f2 == T(0)) continue;
-    const int id12 = P.delta_id[k2 * P.Nk + k1];   // Delta = k2 - k1 -> for P(q1,q2)
-    const int id21 = P.delta_id[k1 * P.Nk + k2];   // Delta = k1 - k2 -> for P(q2,q1)
+    const int id12 = P.delta_id[k2 * P.kstride + k1];   // Delta = k2 - k1 -> for P(q1,q2)
+    const int id21 = P.delta_id[k1 * P.kstride + k2];   // Delta = k1 - k2 -> for P(q2,q1)
     const T* d12 = P.delta + id12 * 3;
     const T* d21 = P.delta + id21 * 3;
     const cplx<T>* bra1 = SD.bra + (size_t)q1 * NN;
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params
     const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
     const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
     for (int sp = 0; sp < 2; ++sp) {
-      if (sp == 1 && !ap_here) continue;
+      if (sp == 1 && (!ap_here || P.h3_only)) continue;
       const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
       const T* U21 = P.tabU + ((size_t)id21 * 2 + sp) * NN;
       const T* U12 = P.tabU + ((size_t)id12 * 2 + sp) * NN;
@@ -612,7 +612,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_occ_pairs_pr(Params
     }
   }
   // 3a2 corrections of this q2: (f2/Nk)/Omega^2 sum_s [c_s F0 + (4 pi A_s/Nk) FT^{-1}[u~_s F_ab]]
-  if (P.div && f2 != T(0)) {
+  if (P.div && f2 != T(0) && !P.h3_only) {
     const T pref = (T)(f2 * P.invOm2);
     const T c0 = (T)(P.corr_c[0] + P.corr_c[1]);
     const cplx<T> cF0 = {(T)(c0 * sF0[0]), (T)(c0 * sF0[1])};

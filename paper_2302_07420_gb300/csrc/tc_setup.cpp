@@ -297,6 +297,9 @@ int smallest_near_best(const double* t, int n) {
 }
 
 static int fft_rep(int m, int n) { return m <= (n - 1) / 2 ? m : m - n; }
+static void value_tables(Setup& S);
+static void build_deltas(Setup& S);
+static void flatten_spheres(Setup& S);
 
 std::string build_setup(const tc_params& p, Setup& S) {
   S.prm = p;
@@ -350,16 +353,9 @@ std::string build_setup(const tc_params& p, Setup& S) {
     if (!sphere(S, S.kcart[k].data(), S.miller[k])) return "plane-wave sphere does not fit the FFT box";
     S.npw[k] = (int)S.miller[k].size();
   }
-  S.npw_max = *std::max_element(S.npw.begin(), S.npw.end());
-  S.miller_flat.assign((size_t)S.Nk * S.npw_max * 3, 0);
-  S.box_index.assign((size_t)S.Nk * S.npw_max, -1);
-  for (int k = 0; k < S.Nk; ++k)
-    for (int g = 0; g < S.npw[k]; ++g) {
-      const auto& m = S.miller[k][g];
-      for (int i = 0; i < 3; ++i) S.miller_flat[((size_t)k * S.npw_max + g) * 3 + i] = m[i];
-      const int i1 = (m[0] + n) % n, i2 = (m[1] + n) % n, i3 = (m[2] + n) % n;
-      S.box_index[(size_t)k * S.npw_max + g] = (i1 * n + i2) * n + i3;
-    }
+  S.Nkt = S.Nk;
+  S.nkb = 0;
+  flatten_spheres(S);
 
   // divergence-correction constant (Eq. correction2, k on the mesh)
   if (p.alpha > 0) {
@@ -380,14 +376,40 @@ std::string build_setup(const tc_params& p, Setup& S) {
   }
   S.Gamma0 = S.Omega / (4.0 * std::sqrt(kPi * kPi * kPi * S.alpha)) - (-S.alpha + aux_sum(S, S.alpha)) / S.Nk;
 
-  // distinct Delta = k_out - k_part
-  std::map<std::tuple<long, long, long>, int> ids;
-  S.delta_id.assign((size_t)S.Nk * S.Nk, 0);
+  S.Nkt = S.Nk;
+  build_deltas(S);
+
+  value_tables(S);
+  return "";
+}
+
+static void value_tables(Setup& S) {
+  KernelData kd;
+  kernel_data(S, KD_VALUE, kd);
+  S.tabV = std::move(kd.tabV);
+  S.tabU = std::move(kd.tabU);
+  S.hartV = std::move(kd.hartV);
+  S.hartU = std::move(kd.hartU);
+  S.hartUs = std::move(kd.hartUs);
+  for (int s = 0; s < 2; ++s) {
+    S.corr_c[s] = kd.corr_c[s];
+    S.amp[s] = kd.amp[s];
+  }
+}
+
+// Distinct Delta = k_out - k_part (unreduced Cartesian differences of the in-cell k of every
+// k-point with orbitals) and the [Nkt][Nkt] id table; pairs of two band points get no id (never used).
+static void build_deltas(Setup& S) {
+  std::map<std::tuple<long long, long long, long long>, int> ids;
+  S.delta_id.assign((size_t)S.Nkt * S.Nkt, 0);
   S.delta.clear();
-  for (int ko = 0; ko < S.Nk; ++ko)
-    for (int kp = 0; kp < S.Nk; ++kp) {
-      long key[3];
-      for (int i = 0; i < 3; ++i) key[i] = std::lround((S.kfrac[ko][i] - S.kfrac[kp][i]) * p.kmesh[i]);
+  for (int ko = 0; ko < S.Nkt; ++ko)
+    for (int kp = 0; kp < S.Nkt; ++kp) {
+      if (ko >= S.Nk && kp >= S.Nk) continue;
+      // mesh differences are integers in units of 1/kmesh; band points are resolved to 2^-20 of that
+      long long key[3];
+      for (int i = 0; i < 3; ++i)
+        key[i] = std::llround((S.kfrac[ko][i] - S.kfrac[kp][i]) * S.prm.kmesh[i] * 1048576.0);
       auto t = std::make_tuple(key[0], key[1], key[2]);
       auto it = ids.find(t);
       int id;
@@ -400,21 +422,51 @@ std::string build_setup(const tc_params& p, Setup& S) {
       } else {
         id = it->second;
       }
-      S.delta_id[(size_t)ko * S.Nk + kp] = id;
+      S.delta_id[(size_t)ko * S.Nkt + kp] = id;
     }
   S.ndelta = (int)S.delta.size();
+}
 
-  KernelData kd;
-  kernel_data(S, KD_VALUE, kd);
-  S.tabV = std::move(kd.tabV);
-  S.tabU = std::move(kd.tabU);
-  S.hartV = std::move(kd.hartV);
-  S.hartU = std::move(kd.hartU);
-  S.hartUs = std::move(kd.hartUs);
-  for (int s = 0; s < 2; ++s) {
-    S.corr_c[s] = kd.corr_c[s];
-    S.amp[s] = kd.amp[s];
+// Flattened Miller vectors and box indices of all Nkt spheres (zero / -1 padded to npw_max).
+static void flatten_spheres(Setup& S) {
+  const int n = S.n;
+  S.npw_max = *std::max_element(S.npw.begin(), S.npw.end());
+  S.miller_flat.assign((size_t)S.Nkt * S.npw_max * 3, 0);
+  S.box_index.assign((size_t)S.Nkt * S.npw_max, -1);
+  for (int k = 0; k < S.Nkt; ++k)
+    for (int g = 0; g < S.npw[k]; ++g) {
+      const auto& m = S.miller[k][g];
+      for (int i = 0; i < 3; ++i) S.miller_flat[((size_t)k * S.npw_max + g) * 3 + i] = m[i];
+      const int i1 = (m[0] + n) % n, i2 = (m[1] + n) % n, i3 = (m[2] + n) % n;
+      S.box_index[(size_t)k * S.npw_max + g] = (i1 * n + i2) * n + i3;
+    }
+}
+
+std::string add_band_points(Setup& S, int nkb, const double* kfrac_band) {
+  if (nkb < 1 || !kfrac_band) return "need at least one band point";
+  if (S.nkb != 0) return "band points already added";
+  S.gamma_b.assign(nkb, 0.0);
+  S.Wb.assign(nkb, {});
+  for (int b = 0; b < nkb; ++b) {
+    std::array<double, 3> f{}, kc{};
+    for (int i = 0; i < 3; ++i) f[i] = kfrac_band[3 * b + i];
+    for (int d = 0; d < 3; ++d) kc[d] = f[0] * S.B[0][d] + f[1] * S.B[1][d] + f[2] * S.B[2][d];
+    double W[3];
+    if (!band_constants(S, kc.data(), &S.gamma_b[b], W))
+      return "band point " + std::to_string(b) + " lies on the SCF mesh (modulo a reciprocal vector)";
+    for (int d = 0; d < 3; ++d) S.Wb[b][d] = W[d];
+    std::vector<std::array<int, 3>> m;
+    if (!sphere(S, kc.data(), m)) return "plane-wave sphere of band point " + std::to_string(b) + " does not fit the FFT box";
+    S.kfrac.push_back(f);
+    S.kcart.push_back(kc);
+    S.miller.push_back(m);
+    S.npw.push_back((int)m.size());
   }
+  S.nkb = nkb;
+  S.Nkt = S.Nk + nkb;
+  flatten_spheres(S);
+  build_deltas(S);
+  value_tables(S);
   return "";
 }
 

@@ -15,6 +15,12 @@ struct Setup {
   double B[3][3]{};        // reciprocal rows b_i, a_i . b_j = 2 pi delta_ij
   double Omega = 0.0;
   int Nk = 0, n = 0, N = 0, nb = 0, no = 0;
+  // band-structure k-points (add_band_points): nkb points after the Nk mesh points carry output
+  // orbitals only; Nkt = Nk + nkb k-points have orbitals (kfrac, kcart, miller, npw, box_index,
+  // and both indices of delta_id run over them)
+  int nkb = 0, Nkt = 0;
+  std::vector<double> gamma_b;                          // [nkb] Gamma_b of each band point
+  std::vector<std::array<double, 3>> Wb;                // [nkb] W of each band point
   std::vector<std::array<double, 3>> kfrac, kcart;
   std::vector<std::vector<std::array<int, 3>>> miller;   // per k, lexicographic
   std::vector<int> npw;
@@ -24,7 +30,7 @@ struct Setup {
   double alpha = 0.0, Gamma0 = 0.0;
   // distinct Delta = k_out - k_part (unreduced)
   int ndelta = 0;
-  std::vector<int> delta_id;                             // [Nk][Nk]
+  std::vector<int> delta_id;                             // [Nkt][Nkt] (row: output k, column: partner k)
   std::vector<std::array<double, 3>> delta;              // Cartesian
   // FP64 tables, all divided by Omega, over the box in global (unpadded) order
   std::vector<double> tabV;    // [ndelta][2][N]  V_2a (right), V_2a^dagger (left), p = 0 value incl. correction
@@ -49,6 +55,11 @@ void kernel_data(const Setup& S, int mode, KernelData& kd);
 
 // Returns an empty string on success, otherwise the reason.
 std::string build_setup(const tc_params& p, Setup& S);
+// Appends nkb band-structure k-points (fractional coordinates kfrac_band[3 b + i]) to a built setup as
+// output-only points: their spheres, the Delta tables of every band/mesh pair and the band constants
+// Gamma_b and W (band_constants).  A point on the SCF mesh modulo a reciprocal vector is refused (it
+// takes the SCF corrections).  Returns an empty string on success, otherwise the reason.
+std::string add_band_points(Setup& S, int nkb, const double* kfrac_band);
 
 // Constants of the divergence corrections at a band-structure k-point off the SCF mesh
 // (Sec. 2.6.3 after Eq. divcorr_2ax_scf; Eqs. divcorr_2ax_band, correction_nabla), for

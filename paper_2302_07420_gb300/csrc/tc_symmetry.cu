@@ -91,7 +91,8 @@ extern "C" {
 
 tc_status tc_set_symmetry(tc_ctx* c, int nops, const int* rot, int time_reversal) {
   if (!c) return TC_ERR_STATE;
-  if (c->batch || !c->ws_owned) return sfail(c, TC_ERR_STATE, "symmetry needs a single-cell context from tc_init");
+  if (c->batch || !c->ws_owned || c->S.nkb > 0)
+    return sfail(c, TC_ERR_STATE, "symmetry needs a single-cell context from tc_init");
   if (nops < 0 || (nops > 0 && !rot)) return sfail(c, TC_ERR_ARG, "bad operation list");
   tc::free_symmetry(c);
   c->sym_ops.clear();

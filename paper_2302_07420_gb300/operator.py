@@ -47,6 +47,9 @@ class Context:
             msg = self.lib.tc_last_error(None)
             raise _lib.TCError(st, msg.decode() if msg else "tc_init failed")
         self.h = h
+        self._finish_init(nbands, nocc)
+
+    def _finish_init(self, nbands, nocc):
         self.nbands, self.nocc = int(nbands), int(nocc)
         nk, npw_max = ctypes.c_int(), ctypes.c_int()
         pn = ctypes.POINTER(ctypes.c_int)()
@@ -63,12 +66,13 @@ class Context:
     def layout(self):
         return self.npw, self.miller
 
-    def _occ(self, occ):
-        occ = np.ascontiguousarray(np.asarray(occ, dtype=np.float64).reshape(self.nk, self.nbands))
+    def _occ(self, occ, nk=None):
+        nk = self.nk if nk is None else nk
+        occ = np.ascontiguousarray(np.asarray(occ, dtype=np.float64).reshape(nk, self.nbands))
         return occ, occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
-    def _check_orbitals(self, x):
-        shape = (self.nk, self.nbands, self.npw_max)
+    def _check_orbitals(self, x, nk=None):
+        shape = (self.nk if nk is None else nk, self.nbands, self.npw_max)
         if tuple(x.shape) != shape:
             raise ValueError("orbital array must have shape %s" % (shape,))
         return x
@@ -283,6 +287,47 @@ def band_layout(lattice, kmesh, ecut, fft, nbands, nocc, A, C, kfrac_band):
     _lib.check(lib, None, lib.tc_band_layout(ctypes.byref(prm), kf.ctypes.data_as(dp), n, m, npw.ctypes.data_as(ip),
                                              miller.ctypes.data_as(ip)))
     return npw, miller
+
+
+class BandContext(Context):
+    """tc_init_band: the operator at band points kfrac_band off the SCF mesh (partners on the mesh).
+
+    ``layout()`` covers the Nk mesh points then the nkb band points with one npw_max; mesh and
+    band-point orbital arrays both use it.
+    """
+
+    def __init__(self, lattice, kmesh, ecut, fft, nbands, nocc, A, C, kfrac_band, alpha=0.0, div_correction=1,
+                 ushort_factor=1.0, precision="fp64", term_mask=0):
+        self.lib = _lib.load()
+        self.params = _lib.make_params(lattice, kmesh, ecut, fft, nbands, nocc, A, C, alpha, div_correction,
+                                       ushort_factor, precision, term_mask)
+        kf = np.ascontiguousarray(np.atleast_2d(kfrac_band), dtype=np.float64)
+        self.nkb = kf.shape[0]
+        h = ctypes.c_void_p()
+        st = self.lib.tc_init_band(ctypes.byref(self.params), self.nkb, kf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   ctypes.byref(h))
+        if st != _lib.TC_OK:
+            msg = self.lib.tc_last_error(None)
+            raise _lib.TCError(st, msg.decode() if msg else "tc_init_band failed")
+        self.h = h
+        self._finish_init(nbands, nocc)
+        self.nk_mesh = self.nk - self.nkb
+
+    def apply_band(self, phi_R, phi_L, occ, band_phi_R, band_phi_L, band_occ, out_R=None, out_L=None, stream=None):
+        """(out_R, out_L) at the band points, [nkb][nbands][npw_max] complex128 on the orbitals' device."""
+        import torch
+        arrs = [self._check_orbitals(x, self.nk_mesh).contiguous() for x in (phi_R, phi_L)]
+        barrs = [self._check_orbitals(x, self.nkb).contiguous() for x in (band_phi_R, band_phi_L)]
+        occ_np, occ_p = self._occ(occ, self.nk_mesh)
+        bocc_np, bocc_p = self._occ(band_occ, self.nkb)
+        if out_R is None:
+            out_R = torch.empty_like(barrs[0])
+        if out_L is None:
+            out_L = torch.empty_like(barrs[1])
+        st = self.lib.tc_apply_band(self.h, _ptr(arrs[0]), _ptr(arrs[1]), occ_p, _ptr(barrs[0]), _ptr(barrs[1]), bocc_p,
+                                    _ptr(out_R), _ptr(out_L), _stream_handle(stream))
+        _lib.check(self.lib, self.h, st)
+        return out_R, out_L
 
 
 class BatchContext:
