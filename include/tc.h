@@ -376,8 +376,17 @@ tc_status tc_alu_peak(int precision, double target_ms, double* tflops, void* cud
  *
  * First call per device: it looks up the device address of the static array
  * (cudaGetSymbolAddress, with that device current) and sets the kernels'
- * shared-memory attributes and FFT twiddle constants; make this first call on
- * each device before any stream capture on that device.
+ * shared-memory attributes and FFT twiddle constants.  With CUDA's lazy module
+ * loading (the default since CUDA 12.2) the array's device memory is taken at
+ * that moment, not when the library is loaded: make the first call on each
+ * device before the host framework reserves its memory pool there, else it can
+ * fail with TC_ERR_CUDA and a reason that names this.  With eager loading
+ * (CUDA_MODULE_LOADING=EAGER) every device that loads the library holds the
+ * array from then on, whether or not the entry point is called.
+ *
+ * Streams: every call uploads its tables and occupations from host memory
+ * that lives only during the call, so it cannot be recorded into a CUDA graph;
+ * a call on a stream that is capturing returns TC_ERR_STATE before any work.
  *
  * Sharing: all calls on a device use the same array, which keeps the
  * previous call's contents (each call clears what must start at zero).  Calls

@@ -139,6 +139,20 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   if (!out_R && !out_L) return TC_OK;
   if (const int f = tc::injected_fault("launch")) return fail((tc_status)f, "injected fault (TC_FAULT): no device work done");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the per-call uploads read host memory that lives only during the call: not capturable
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      // the legacy default stream while another stream captures in global mode
+      if (ce == cudaErrorStreamCaptureImplicit)
+        return fail(TC_ERR_STATE, "a graph capture is in progress: the per-call host uploads cannot be captured");
+      return fail(TC_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(ce));
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(TC_ERR_STATE, "the stream is capturing a graph: the per-call host uploads cannot be captured");
+  }
   tc_ctx c;
   const std::string why = tc::build_setup(*params, c.S);
   if (!why.empty()) return fail(why.rfind("unsupported", 0) == 0 ? TC_ERR_UNSUPPORTED : TC_ERR_ARG, why);
@@ -178,7 +192,12 @@ extern "C" tc_status tc_apply_noalloc(const tc_params* params, const void* phi_R
   {
     std::lock_guard<std::mutex> lock(g_mu);
     base = static_cast<char*>(arena_address(dev, e));
-    if (!base) return fail(TC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    if (!base)
+      return fail(TC_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e) +
+                                   (e == cudaErrorMemoryAllocation
+                                        ? " (the static array is placed in device memory at the first call on a device "
+                                          "under lazy module loading: make that call before reserving device memory)"
+                                        : ""));
     const unsigned bit = 1u << ((f64 ? 0 : 16) + size_slot(S.n));
     if (!(g_prepared[dev] & bit)) {
       const int r = f64 ? prepare<double>(&c, S.n) : prepare<float>(&c, S.n);

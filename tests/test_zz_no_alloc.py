@@ -91,3 +91,74 @@ def test_noalloc_rejects_problems_beyond_the_static_array():
                               None, None)
     assert st == _lib.TC_ERR_UNSUPPORTED
     assert b"TC_NOALLOC_MAX_BYTES" in lib.tc_last_error(None)
+
+
+def test_noalloc_larger_smaller_larger_and_one_side_keep_matching_tc_apply():
+    """One process: a 16^3 FP64 case, a 9^3 FP32 case, the 16^3 case again (the shared array holds the
+    smaller call's contents in between), and one call with out_L = NULL; each equals tc_apply.  Free
+    device memory does not change from one call to the next: the calls allocate nothing."""
+    from paper_2302_07420_gb300.operator import Context
+    lib = _lib.load()
+    runs = []
+    for name, prec, make in (CASES[2], CASES[1]):
+        p = make()
+        c_phi, c_chi, occ = _inputs(p, len(name))
+        d_phi, d_chi = torch.from_numpy(c_phi).cuda(), torch.from_numpy(c_chi).cuda()
+        ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                      precision=prec)
+        ref_r, ref_l = ctx.apply(d_phi, d_chi, occ)
+        torch.cuda.synchronize()
+        ctx.close()
+        prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"],
+                               p["C"], precision=prec)
+        runs.append((name, prec, prm, d_phi, d_chi, np.ascontiguousarray(occ, dtype=np.float64),
+                     ref_r.cpu().numpy(), ref_l.cpu().numpy(), torch.empty_like(d_phi), torch.empty_like(d_chi)))
+    torch.cuda.synchronize()
+    free = []
+    for i in (0, 1, 0, 0):
+        name, prec, prm, d_phi, d_chi, occ, ref_r, ref_l, out_r, out_l = runs[i]
+        one_side = len(free) == 3
+        st = lib.tc_apply_noalloc(ctypes.byref(prm), ctypes.c_void_p(d_phi.data_ptr()),
+                                  ctypes.c_void_p(d_chi.data_ptr()),
+                                  occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ctypes.c_void_p(out_r.data_ptr()),
+                                  None if one_side else ctypes.c_void_p(out_l.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        _lib.check(lib, None, st)
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info()[0])
+        scale = max(np.abs(ref_r).max(), np.abs(ref_l).max())
+        err = np.abs(out_r.cpu().numpy() - ref_r).max() / scale
+        if not one_side:
+            err = max(err, np.abs(out_l.cpu().numpy() - ref_l).max() / scale)
+        assert err <= TOL[prec], (name, len(free), err)
+    assert free[1] == free[2] == free[3], free
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The per-call uploads read host memory that lives only during the call: a call on a stream that
+    is capturing a graph returns TC_ERR_STATE before any work."""
+    name, prec, make = CASES[1]
+    p = make()
+    c_phi, c_chi, occ = _inputs(p, len(name))
+    d_phi, d_chi = torch.from_numpy(c_phi).cuda(), torch.from_numpy(c_chi).cuda()
+    out_r, out_l = torch.empty_like(d_phi), torch.empty_like(d_chi)
+    occ = np.ascontiguousarray(occ, dtype=np.float64)
+    lib = _lib.load()
+    prm = _lib.make_params(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
+                           precision=prec)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            st = lib.tc_apply_noalloc(ctypes.byref(prm), ctypes.c_void_p(d_phi.data_ptr()),
+                                      ctypes.c_void_p(d_chi.data_ptr()),
+                                      occ.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      ctypes.c_void_p(out_r.data_ptr()), ctypes.c_void_p(out_l.data_ptr()),
+                                      ctypes.c_void_p(s.cuda_stream))
+        finally:
+            g.capture_end()
+    assert st == _lib.TC_ERR_STATE
+    assert b"capturing" in lib.tc_last_error(None)
