@@ -4,7 +4,8 @@ Cells from the HEG batch recipe (synth.heg_batch: uneven boxes 16^3-32^3,
 1-8 k-points, 7-33 plane waves per k), FP32:
 * every cell's output equals a single-cell tc_apply of the same inputs bit for bit;
 * plane-wave orbitals: every output is diagonal in momentum and out_L = out_R (BITC = TC);
-* the two cheapest cells against the FP64 oracle (1e-5);
+* the two cheapest cells against the FP64 oracle (1e-5), and for every box size of the recipe the
+  cheapest cell of the 256, batched together, against the oracle (1e-5);
 * a second call replays the captured graph with identical results;
 * error paths of the batch API.
 """
@@ -114,3 +115,33 @@ def test_batch_error_paths(batch):
     assert lib.tc_init_batch(2, prm, ctypes.byref(h)) == _lib.TC_ERR_ARG
     with pytest.raises(_lib.TCError):
         bc.apply([torch.from_numpy(c) for _, c, _ in data], d, [o for _, _, o in data])   # host arrays
+
+
+def test_one_cell_of_every_box_size_against_the_oracle():
+    """For each box size of the 256-cell recipe (16^3 .. 32^3: shared-memory, pruned-free and
+    global-scratch kernels) the cheapest cell, the eight batched in one graph, against the oracle."""
+    from paper_2302_07420_gb300.operator import BatchContext
+    allc = synth.heg_batch(256)
+    best = {}
+    for i, p in enumerate(allc):
+        n = p["fft"][0]
+        cost = int(np.prod(p["kmesh"])) ** 2 * p["nocc"] ** 2 * n ** 3
+        if n not in best or cost < best[n][1]:
+            best[n] = (i, cost)
+    sizes = sorted(best)
+    assert sizes == [16, 18, 20, 24, 25, 27, 30, 32]
+    cells = [allc[best[n][0]] for n in sizes]
+    data = _inputs(cells)
+    bc = BatchContext(cells, precision="fp32")
+    try:
+        d = [torch.from_numpy(c).cuda() for _, c, _ in data]
+        out_r, out_l = bc.apply(d, d, [o for _, _, o in data])
+        torch.cuda.synchronize()
+        res = [(r.cpu().numpy(), l.cpu().numpy()) for r, l in zip(out_r, out_l)]
+    finally:
+        bc.close()
+    for n, (S, c, occ), (r, l) in zip(sizes, data, res):
+        ref_r, ref_l = OP.tc_apply(S, c, c, occ)
+        scale = np.abs(ref_r).max()
+        assert np.abs(r - ref_r).max() / scale < 1e-5, n
+        assert np.abs(l - ref_l).max() / scale < 1e-5, n
