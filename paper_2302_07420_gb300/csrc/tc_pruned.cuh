@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
   using G = Geo<N>;
   using S = Sup<N, L>;
   using SM = PrSmem<T, N, L, 2, 3>;
-  constexpr int CH = 1;   // elements per load chunk of the pointwise pass (1: measured fastest in FP32 and FP64)
+  constexpr int CH = 1;   // elements per load chunk of the pointwise pass (1 measured fastest in FP32)
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T red[32];
   const SideArgs<T>& SD = P.side[blockIdx.y];
