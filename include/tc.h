@@ -273,6 +273,19 @@ tc_status tc_autotune(tc_ctx* ctx, const void* phi_R, const void* phi_L, const d
                       int* sc_out, void* cuda_stream);
 /* ms[i] = accumulated device time of stage i (ms), launches[i] = kernel launches; n >= TC_NSTAGES. */
 tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
+/* tc_pair_kernels -- which kernels the pair stages of this context's applies run (the fused pair
+ * chains of Algs. 2, 5, 6, 9, 11, 12; the 3b4 pass of Alg. 10; the occupied-pair stage of Algs. 4,
+ * 6, 8, 11).  For each of the three, in that order, info[3 i .. 3 i + 2] =
+ *   kind:    0 full transforms, one CTA per item; 1 transforms pruned to the pair-density
+ *            support, one CTA per item; 2 transforms on the support (or full) split over a
+ *            thread-block cluster, the volumes in the CTAs' distributed shared memory
+ *   support: transform points per axis on the spectral side (the box size n for full transforms)
+ *   ctas:    CTAs per item (the cluster width; 1 for kinds 0 and 1)
+ * The choice follows from the box size, the precision, the Miller span of the spheres (support
+ * 2 span + 1) and whether the device can hold the kernel's cluster; every kind computes the same
+ * operator.  info: 9 ints (host).  Errors: TC_ERR_STATE (null context, or a batch: ask its cells,
+ * tc_batch_cell), TC_ERR_ARG (null info). */
+tc_status tc_pair_kernels(const tc_ctx* ctx, int* info);
 
 /* tc_band_constants -- the constants of the divergence corrections at
  * band-structure k-points off the SCF mesh (Sec. 2.6.3 after Eq.

@@ -21,7 +21,8 @@ EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy",
             "tc_last_error", "tc_destroy", "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
             "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
             "tc_davidson_step", "tc_set_symmetry", "tc_symmetry_info", "tc_symmetrize_orbitals", "tc_autotune",
-            "tc_alu_peak", "tc_band_constants", "tc_band_layout", "tc_init_band", "tc_apply_band")
+            "tc_alu_peak", "tc_band_constants", "tc_band_layout", "tc_init_band", "tc_apply_band",
+            "tc_pair_kernels")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",

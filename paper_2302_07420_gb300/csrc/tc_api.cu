@@ -1120,6 +1120,25 @@ tc_status tc_stage_times(const tc_ctx* c, double* ms, int* launches, int n) {
   return TC_OK;
 }
 
+tc_status tc_pair_kernels(const tc_ctx* c, int* info) {
+  if (!c || c->batch) return TC_ERR_STATE;
+  if (!info) return TC_ERR_ARG;
+  // the dispatch rule of run_pipeline
+  const bool pruned = c->plan_prune_L > 0 && c->pair_support <= c->plan_prune_L;
+  const bool dist = !pruned && c->plan_cl_L > 0 && c->pair_support <= c->plan_cl_L;
+  for (int k = 0; k < 3; ++k) {
+    int* o = info + 3 * k;
+    if (pruned) {
+      o[0] = 1; o[1] = c->plan_prune_L; o[2] = 1;
+    } else if (dist && c->plan_cl[k] > 0 && ((c->cluster_ok >> k) & 1)) {
+      o[0] = 2; o[1] = c->plan_cl_L; o[2] = c->plan_cl[k];
+    } else {
+      o[0] = 0; o[1] = c->S.n; o[2] = 1;
+    }
+  }
+  return TC_OK;
+}
+
 const char* tc_last_error(const tc_ctx* c) { return c ? c->err.c_str() : g_init_err.c_str(); }
 
 tc_status tc_destroy(tc_ctx* c) {

@@ -77,6 +77,13 @@ struct tc_ctx {
   // box indices per axis that a pair-density spectrum can occupy (tc::pair_support_len); the pair
   // chains use their pruned transforms when it fits the compiled support length (large: never)
   int pair_support = 1 << 30;
+  // cluster-distributed pair kernels that can be scheduled on this device (bit 0 chain, 1 3b4,
+  // 2 occupied pairs; tc_cluster.cuh), set by prepare_kernels
+  int cluster_ok = 0;
+  // compiled plans of the box: support length of the one-CTA pruned kernels (0: none), of the
+  // cluster kernels (0: none) and the cluster widths of the chain, 3b4 and occupied-pair kernels
+  int plan_prune_L = 0, plan_cl_L = 0;
+  int plan_cl[3] = {0, 0, 0};
   // output orbitals of an apply: Nk nb at the mesh points, or nkb nb at the band points of a band
   // context (tc_init_band); band h3 chunks; band constants [nkb][4] = (W, Gamma_b) and the band
   // correction scalars [2][nkb][nocc][nbands][kBandScalars] (device)

@@ -7,6 +7,7 @@
 #include "tc_ctx.hpp"
 #include "tc_kernels_impl.cuh"
 #include "tc_pruned.cuh"
+#include "tc_cluster.cuh"
 #include "tc_band.cuh"
 
 namespace tc {
@@ -104,6 +105,50 @@ template <typename T, int N> static inline int smem_vols(int want, int static_by
     }                                                                                         \
   } while (0)
 
+// Launch of a cluster-distributed kernel: clusters of cl CTAs along x (grid.x a multiple of cl).
+template <typename... Args>
+static cudaError_t launch_cluster(void (*kern)(Args...), dim3 grid, int threads, size_t smem, int cl,
+                                  cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Sets the kernel's shared-memory size and reports whether one cluster of it fits the device.
+template <typename K> static bool cluster_fits(tc_ctx*, K kern, int cl, int threads, size_t smem) {
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
 template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
   // twiddles exp(-2 pi i j/L) for every codelet length, FP64 host sin/cos
   static double tw64[2 * kTwTotal];
@@ -142,6 +187,22 @@ template <typename T, int N> int prepare_kernels(tc_ctx* ctx) {
   }
   TC_SET_SMEM((k_fft3d<T, N, -1>), vb1);
   TC_SET_SMEM((k_fft3d<T, N, +1>), vb1);
+  // cluster-distributed kernels: each is used only if the device can hold one of its clusters
+  ctx->cluster_ok = 0;
+  using C0 = ClCfg<T, N, 0>;
+  using C1 = ClCfg<T, N, 1>;
+  using C2 = ClCfg<T, N, 2>;
+  ctx->plan_prune_L = kPruneL<N> < N ? kPruneL<N> : 0;
+  ctx->plan_cl_L = ClPlan<T, N>::L;
+  ctx->plan_cl[0] = C0::CL;
+  ctx->plan_cl[1] = C1::CL;
+  ctx->plan_cl[2] = C2::CL;
+  if constexpr (C0::CL > 0)
+    ctx->cluster_ok |= cluster_fits(ctx, k_pair_chain_cl<T, N>, C0::CL, C0::threads, C0::smem) ? 1 : 0;
+  if constexpr (C1::CL > 0)
+    ctx->cluster_ok |= cluster_fits(ctx, k_pair_3b4_cl<T, N>, C1::CL, C1::threads, C1::smem) ? 2 : 0;
+  if constexpr (C2::CL > 0)
+    ctx->cluster_ok |= cluster_fits(ctx, k_occ_pairs_cl<T, N>, C2::CL, C2::threads, C2::smem) ? 4 : 0;
   return TC_OK;
 }
 
@@ -163,6 +224,16 @@ template <typename T, int N> size_t scratch_needed(const Setup& S, int so_max, i
     cudaError_t e_ = cudaGetLastError();                                                      \
     if (e_ != cudaSuccess) {                                                                  \
       ctx->err = std::string(name) + ": " + cudaGetErrorString(e_);                           \
+      return TC_ERR_CUDA;                                                                     \
+    }                                                                                         \
+  } while (0)
+
+#define TC_CHECK_CL(call)                                                                     \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                     \
+      ctx->err = std::string("cluster launch: ") + cudaGetErrorString(e_);                    \
       return TC_ERR_CUDA;                                                                     \
     }                                                                                         \
   } while (0)
@@ -218,6 +289,16 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
   // pair densities whose spectra fit the compiled support take the pruned transforms
   constexpr int LP = kPruneL<N>;
   const bool pruned = LP < N && ctx->pair_support <= LP;
+  // else, when they fit the distributed kernels' support, the cluster-distributed ones
+  constexpr int LC = ClPlan<T, N>::L;
+  using C0 = ClCfg<T, N, 0>;
+  using C1 = ClCfg<T, N, 1>;
+  using C2 = ClCfg<T, N, 2>;
+  constexpr int CLc = C0::CL, CLb = C1::CL, CLo = C2::CL;
+  const bool dist = !pruned && LC > 0 && ctx->pair_support <= LC;
+  const bool dist_chain = dist && CLc > 0 && (ctx->cluster_ok & 1);
+  const bool dist_3b4 = dist && CLb > 0 && (ctx->cluster_ok & 2);
+  const bool dist_occ = dist && CLo > 0 && (ctx->cluster_ok & 4);
   // 1. orbitals to real space
   stage_mark(ctx, st, 0);
   k_orbitals<T, N><<<dim3(nj_all, 4, 2), TH, vb1, st>>>(cphi, cchi, bphi, bchi, nj, ctx->d_box_index, ctx->d_kpg,
@@ -297,7 +378,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
         k_occ_pairs_pr<T, N, LP><<<dim3(q2_items * Pa.so, occ_sides), PrCfg<T, N>::threads,
                                    OccSmem<T, N, LP>::bytes, st>>>(Pa);
     }
-    if (!pruned) k_occ_pairs<T, N><<<dim3(q2_items * Pa.so, occ_sides), TH, Pa.nsmem * vb, st>>>(Pa);
+    if constexpr (CLo > 0) {
+      if (dist_occ)
+        TC_CHECK_CL(launch_cluster(k_occ_pairs_cl<T, N>, dim3(q2_items * Pa.so * CLo, occ_sides), C2::threads,
+                                   C2::smem, CLo, st, Pa));
+    }
+    if (!pruned && !dist_occ) k_occ_pairs<T, N><<<dim3(q2_items * Pa.so, occ_sides), TH, Pa.nsmem * vb, st>>>(Pa);
     TC_CHECK_LAUNCH("k_occ_pairs");
     if (Pa.so > 1) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, occ_sides), 256, 0, st>>>(Pa, 0);
@@ -340,7 +426,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
       if (pruned)
         k_occ_pairs_pr<T, N, LP><<<dim3(Pq.nq2 * Pq.so, 2), PrCfg<T, N>::threads, OccSmem<T, N, LP>::bytes, st>>>(Pq);
     }
-    if (!pruned) k_occ_pairs<T, N><<<dim3(Pq.nq2 * Pq.so, 2), TH, Pq.nsmem * vb, st>>>(Pq);
+    if constexpr (CLo > 0) {
+      if (dist_occ)
+        TC_CHECK_CL(launch_cluster(k_occ_pairs_cl<T, N>, dim3(Pq.nq2 * Pq.so * CLo, 2), C2::threads, C2::smem, CLo,
+                                   st, Pq));
+    }
+    if (!pruned && !dist_occ) k_occ_pairs<T, N><<<dim3(Pq.nq2 * Pq.so, 2), TH, Pq.nsmem * vb, st>>>(Pq);
     TC_CHECK_LAUNCH("k_occ_pairs (band points)");
     if (Pq.so > 1) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, 2), 256, 0, st>>>(Pq, 0);
@@ -370,7 +461,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
         k_pair_chain_pr<T, N, LP><<<dim3(nj_items * P.sc, nsides), PrCfg<T, N>::threads,
                                     PrSmem<T, N, LP, 2, 3>::bytes, st>>>(Pc);
     }
-    if (!pruned) k_pair_chain<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
+    if constexpr (CLc > 0) {
+      if (dist_chain)
+        TC_CHECK_CL(launch_cluster(k_pair_chain_cl<T, N>, dim3(nj_items * P.sc * CLc, nsides), C0::threads,
+                                   C0::smem, CLc, st, Pc));
+    }
+    if (!pruned && !dist_chain) k_pair_chain<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pc.nsmem * vb, st>>>(Pc);
     TC_CHECK_LAUNCH("k_pair_chain");
     stage_mark(ctx, st, 4);
     if (P.sc > 1) {
@@ -392,7 +488,12 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
         k_pair_3b4_pr<T, N, LP><<<dim3(nj_items * P.sc, nsides), PrCfg<T, N>::threads,
                                   PrSmem<T, N, LP, 1, 1>::bytes, st>>>(Pb);
     }
-    if (!pruned) k_pair_3b4<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
+    if constexpr (CLb > 0) {
+      if (dist_3b4)
+        TC_CHECK_CL(launch_cluster(k_pair_3b4_cl<T, N>, dim3(nj_items * P.sc * CLb, nsides), C1::threads, C1::smem,
+                                   CLb, st, Pb));
+    }
+    if (!pruned && !dist_3b4) k_pair_3b4<T, N><<<dim3(nj_items * P.sc, nsides), TH, Pb.nsmem * vb, st>>>(Pb);
     TC_CHECK_LAUNCH("k_pair_3b4");
     if (P.sc > 1 && tw[T3B4] != 0) {
       k_sum_parts<T, N><<<dim3(2 * pw_blocks, nsides), 256, 0, st>>>(P, 2);

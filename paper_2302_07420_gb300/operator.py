@@ -224,6 +224,13 @@ class Context:
         _lib.check(self.lib, self.h, self.lib.tc_stage_times(self.h, ms, nl, _lib.TC_NSTAGES))
         return {s: (ms[i], nl[i]) for i, s in enumerate(_lib.STAGES)}
 
+    def pair_kernels(self):
+        """{stage: (kind, support, ctas)} of the pair chains, the 3b4 pass and the occupied-pair stage
+        (kind 0 full transforms, 1 pruned, 2 on thread-block clusters; tc_pair_kernels)."""
+        info = (ctypes.c_int * 9)()
+        _lib.check(self.lib, self.h, self.lib.tc_pair_kernels(self.h, info))
+        return {s: tuple(info[3 * i: 3 * i + 3]) for i, s in enumerate(("pair_chain", "pair_3b4", "occ_pairs"))}
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.tc_destroy(self.h)

@@ -88,7 +88,8 @@ def test_layout_matches_oracle(name):
 
 
 CASES = [(0, (1, 1, 2), 9), (1, (2, 1, 1), 12), (2, (1, 2, 2), 15)]
-# boxes beyond 24^3 keep some or all work volumes in global memory instead of shared memory
+# 18^3 and 20^3 keep some work volumes in global memory; from 25^3 up these small spheres take the
+# pair kernels on thread-block clusters (test_gpu_cluster.py)
 LARGE = [(3, (1, 1, 2), 18), (4, (1, 1, 1), 20), (5, (1, 2, 1), 25), (6, (1, 1, 2), 27), (7, (1, 1, 1), 30),
          (8, (2, 1, 1), 32)]
 

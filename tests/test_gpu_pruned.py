@@ -2,10 +2,11 @@
 
 At 24^3 the library runs the pair chains and the 3b4 pass with transforms restricted to the
 pair-density support (17 box indices per axis) when the Miller span s of the spheres gives
-2 s + 1 <= 17, and the full transforms otherwise.  The cases cover small supports (span 2 and 6),
-the edge 2 s + 1 = 17 (the silicon-like cell at 7.5 Ha, the bench cell's spheres), and a span
-beyond it (10 Ha, full transforms), every term separately in FP64 and the totals in both
-precisions.  Tolerances are those of the other parity tests.
+2 s + 1 <= 17, on thread-block clusters with support 21 up to 2 s + 1 = 21, and with full
+transforms beyond.  The cases cover small supports (span 2 and 6), the edge 2 s + 1 = 17 (the
+silicon-like cell at 7.5 Ha, the bench cell's spheres), and a span beyond it (10 Ha, the cluster
+kernels; test_gpu_cluster.py covers them and the full transforms), every term separately in FP64 and
+the totals in both precisions.  Tolerances are those of the other parity tests.
 """
 import numpy as np
 import pytest
@@ -32,7 +33,7 @@ def _case(name):
         p = synth.tiny_params(11, kmesh=(1, 1, 2), fft=(24,) * 3, ecut=6.0, nbands=3, nocc=2, scale=5.0)
     elif name == "si_k112_edge":
         p = synth.si_params(kmesh=(1, 1, 2), nbands=3, nocc=2)
-    else:   # "si_k112_wide": span 10, full transforms
+    else:   # "si_k112_wide": span 10, beyond the one-CTA pruned support
         p = synth.si_params(kmesh=(1, 1, 2), ecut=10.0, nbands=3, nocc=2)
     S = make_setup(p)
     c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 400 + len(name), [S.kpG(k) for k in range(S.Nk)],
