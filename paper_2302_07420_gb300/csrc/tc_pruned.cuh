@@ -35,8 +35,10 @@ template <int N, int L> struct Sup {
   static __device__ __forceinline__ int cidx(int c1, int c2, int c3) { return (c1 * L + c2) * L + c3; }
 };
 
-// Support length of the pruned kernels compiled for box size N (N: not compiled pruned).
-template <int N> constexpr int kPruneL = (N == 24) ? 17 : N;
+// Support length of the pruned kernels compiled for box size N (N: not compiled pruned): 17 at 24^3
+// (the silicon-like 4x4x4 cell's spheres) and the supports 4 floor((N-1)/4) + 1 of the batched HEG
+// cells' spheres at 16^3, 18^3 and 20^3.
+template <int N> constexpr int kPruneL = (N == 16) ? 13 : (N == 18 || N == 20 || N == 24) ? 17 : N;
 
 // Threads per CTA of the pruned kernels: one axis-1 pencil per thread in FP32, two in FP64
 // (a pencil of N double-complex values takes 4 N registers).
