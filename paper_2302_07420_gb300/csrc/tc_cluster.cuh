@@ -26,8 +26,9 @@ namespace tc {
 
 namespace cg = cooperative_groups;
 
-// One kernel's cluster configuration: CTAs per cluster, whether the compact spectra sit in shared
-// memory (else in the item's scratch slice, each CTA touching its own rows only), the CTAs per SM its
+// One kernel's cluster configuration: CTAs per cluster, which compact spectra sit in shared memory
+// (spec 1: all; 2: the chain's pair spectrum A only, its accumulator C in the scratch slice; 0: none,
+// the spectra in the item's scratch slice, each CTA touching its own rows only), the CTAs per SM its
 // launch bounds ask for, the threads per CTA (0: one axis-1 pencil per thread), and the elements per
 // load chunk of the chain's pointwise pass (its loads for a chunk are issued together).
 struct ClChoice {
@@ -37,11 +38,12 @@ struct ClChoice {
 // Cluster plan for box size N: the support length L of the distributed kernels (0: none built; the
 // pair-density support of spheres |m| <= r is 4 r + 1, which the plan covers for the boxes of the
 // batched HEG cells, 4 floor((N-1)/4) + 1, and with full transforms at 48^3) and the choice per kernel
-// (kind 0 pair chain, 1 3b4 pass, 2 occupied pairs).  FP32 takes the choices below, made for 12-18
-// resident warps per SM (one axis-1 pencil per thread: warps per SM = CTAs per SM x pencils per CTA
-// / 32, bounded by the shared memory of the row slices and by the registers a pencil needs -- a 32-point
-// FP32 chain fits 128 registers, the occupied-pair kernel needs about 168).  FP64 takes the smallest
-// width whose slices fit one CTA per SM (with the spectra if they fit too), one CTA per SM.
+// (kind 0 pair chain, 1 3b4 pass, 2 occupied pairs).  FP32 takes the choices below, each the fastest of
+// the configurations timed per box on the batched HEG cells (2, 3, 4, 6 or 8 CTAs; spectra on chip or
+// in L2; 1-3 CTAs per SM; load chunks of 1, 2 or 4): few CTAs per cluster with the spectra on chip
+// where they fit generally won over more warps per SM from more, smaller CTAs, whose rows are mostly
+// remote and whose barriers have more participants.  FP64 takes the smallest width whose slices fit
+// one CTA per SM (with the spectra if they fit too).
 template <typename T, int N> struct ClPlan {
   static constexpr int L = (N == 24) ? 21 : (N == 25 || N == 27) ? 25 : (N == 30 || N == 32) ? 29 : (N == 48) ? 48 : 0;
   static constexpr int P = N | 1;
@@ -54,11 +56,12 @@ template <typename T, int N> struct ClPlan {
     return ((t + 31) / 32) * 32;
   }
   static constexpr int nspec(int kind) { return kind == 1 ? 1 : 2; }
-  // bytes of the row slices: work rows (and, for kind 2, B1 by pencil), then the spectra if spec
+  // bytes of the row slices: work rows (and, for kind 2, B1 by pencil), then the spectra on chip
   static constexpr size_t bytes(int kind, int cl, int spec) {
     const size_t b = (size_t)rows(cl) * N * P * z;
     const size_t base = kind == 2 ? (size_t)N * pens(cl) * z + b : b;
-    return base + (spec ? (size_t)nspec(kind) * rows(cl) * L * L * z : 0);
+    const int on_chip = spec == 1 ? nspec(kind) : (spec == 2 ? 1 : 0);
+    return base + (size_t)on_chip * rows(cl) * L * L * z;
   }
   static constexpr ClChoice choice64(int kind) {
     if (L == 0) return ClChoice{0, 0, 0, 0, 1};
@@ -72,11 +75,11 @@ template <typename T, int N> struct ClPlan {
     if (sizeof(T) == 8) return choice64(kind);
     switch (N) {
       case 24: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : ClChoice{2, 1, 1, 0, 1};
-      case 25: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{4, 0, 2, 0, 1});
-      case 27: return kind == 0 ? ClChoice{2, 1, 1, 0, 2} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{4, 0, 2, 0, 1});
-      case 30: return kind == 0 ? ClChoice{2, 0, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{4, 1, 1, 0, 1});
-      case 32: return kind == 0 ? ClChoice{2, 0, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{4, 0, 1, 0, 1});
-      case 48: return kind == 0 ? ClChoice{4, 0, 1, 288, 4} : (kind == 1 ? ClChoice{8, 1, 1, 0, 1} : ClChoice{8, 0, 1, 0, 1});
+      case 25: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
+      case 27: return kind == 0 ? ClChoice{2, 1, 1, 0, 2} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
+      case 30: return kind == 0 ? ClChoice{2, 2, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
+      case 32: return kind == 0 ? ClChoice{2, 2, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{3, 0, 1, 0, 1});
+      case 48: return kind == 0 ? ClChoice{4, 0, 1, 288, 4} : (kind == 1 ? ClChoice{6, 0, 1, 0, 1} : ClChoice{8, 0, 1, 0, 1});
       default: return ClChoice{0, 0, 0, 0, 1};
     }
   }
@@ -87,19 +90,22 @@ template <typename T, int N, int KIND> struct ClCfg {
   using PL = ClPlan<T, N>;
   static constexpr int L = PL::L;
   static constexpr int CL = PL::choice(KIND).cl;
-  static constexpr bool SPEC = PL::choice(KIND).spec != 0;
+  static constexpr bool SPEC = PL::choice(KIND).spec == 1;     // every spectrum on chip
+  static constexpr bool SPEC_A = PL::choice(KIND).spec != 0;   // the (first) pair spectrum on chip
   static constexpr int MINB = PL::choice(KIND).minb;
   static constexpr int CH = PL::choice(KIND).ch;
   // one axis-1 pencil per thread unless the choice caps the count; FP64 at most 256 threads (a double
   // pencil takes 4 N registers); the passes loop over their pencils, so any count is correct
   static constexpr int want = PL::choice(KIND).thr > 0 ? PL::choice(KIND).thr : PL::need(CL);
   static constexpr int threads = (sizeof(T) == 8 && want > 256) ? 256 : want;
-  static constexpr size_t bytes = PL::bytes(KIND, CL, SPEC ? 1 : 0);
+  static constexpr size_t bytes = PL::bytes(KIND, CL, PL::choice(KIND).spec);
   // kernel-table rows of the current Delta (3 for the chain, 1 for 3b4) when they fit as well
   static constexpr size_t tab_bytes = (size_t)(KIND == 0 ? 3 : 1) * PL::rows(CL) * L * L * sizeof(T);
-  static constexpr bool tab = KIND != 2 && SPEC && (size_t)MINB * (bytes + tab_bytes + 2048) <= 233472;
+  static constexpr bool tab = (KIND == 0 ? SPEC : (KIND == 1 && SPEC_A)) &&
+                              (size_t)MINB * (bytes + tab_bytes + 2048) <= 233472;
   static constexpr size_t smem = bytes + (tab ? tab_bytes : 0);
   static_assert(CL == 0 || (size_t)MINB * (smem + 2048) <= 233472, "row slices exceed the SM's shared memory");
+  static_assert(KIND != 2 || PL::choice(KIND).spec != 2, "the occupied-pair kernel keeps both spectra or none");
 };
 
 // Row slices of one CTA (rank r: compact rows [r R, r R + R) and axis-1 pencils [r PEN, r PEN + PEN)).
@@ -236,14 +242,18 @@ __global__ void __launch_bounds__(ClCfg<T, N, 0>::threads, ClCfg<T, N, 0>::MINB)
   cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* A;
   cplx<T>* C;
+  // this CTA's rows of the item's compact spectra in its scratch slots (k_pair_chain's, one item each)
+  const size_t item = (size_t)blockIdx.y * (gridDim.x / CL) + blockIdx.x / CL;
+  cplx<T>* gA = P.scratch + item * 3 * (size_t)Geo<N>::vol + (size_t)c1_0 * L * L;
   if constexpr (SM::SPEC) {
     A = B + D::bslab;
     C = A + D::cslab;
+  } else if constexpr (SM::SPEC_A) {
+    A = B + D::bslab;
+    C = gA + Sup<N, L>::cvol;
   } else {
-    // this CTA's rows of the item's compact spectra (scratch slots of k_pair_chain, one item each)
-    const size_t item = (size_t)blockIdx.y * (gridDim.x / CL) + blockIdx.x / CL;
-    A = P.scratch + item * 3 * (size_t)Geo<N>::vol + (size_t)c1_0 * L * L;
-    C = A + Sup<N, L>::cvol;
+    A = gA;
+    C = gA + Sup<N, L>::cvol;
   }
   T* tU = SM::tab ? reinterpret_cast<T*>(C + D::cslab) : nullptr;
   cplx<T>* rb[CL];
@@ -453,7 +463,7 @@ __global__ void __launch_bounds__(ClCfg<T, N, 1>::threads, ClCfg<T, N, 1>::MINB)
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* A;
-  if constexpr (SM::SPEC) {
+  if constexpr (SM::SPEC_A) {
     A = B + D::bslab;
   } else {
     const size_t item = (size_t)blockIdx.y * (gridDim.x / CL) + blockIdx.x / CL;

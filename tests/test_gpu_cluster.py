@@ -119,14 +119,14 @@ def test_cluster_total(name, prec):
 
 def test_cluster_plan_is_reported():
     """tc_pair_kernels: the one-CTA pruned kernels at 24^3 for spans up to 8, clusters for the three
-    pair kernels at 32^3 in FP32 (2, 2 and 4 CTAs), full transforms beyond the compiled support."""
+    pair kernels at 32^3 in FP32 (2, 2 and 3 CTAs), full transforms beyond the compiled support."""
     p, *_ = _ref("c32_span8")
     ctx = _ctx(p, precision="fp32")
     try:
         info = ctx.pair_kernels()
     finally:
         ctx.close()
-    assert info == {"pair_chain": (2, 29, 2), "pair_3b4": (2, 29, 2), "occ_pairs": (2, 29, 4)}, info
+    assert info == {"pair_chain": (2, 29, 2), "pair_3b4": (2, 29, 2), "occ_pairs": (2, 29, 3)}, info
     p = synth.si_params(kmesh=(1, 1, 2), nbands=3, nocc=2)      # span 8 at 24^3
     ctx = _ctx(p, precision="fp32")
     try:
