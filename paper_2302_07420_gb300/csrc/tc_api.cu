@@ -96,7 +96,7 @@ template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t&
 void free_all(tc_ctx* c) {
   void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
                   c->d_hartU, c->d_hartUs, c->d_occ, c->ws_owned ? c->d_ws : nullptr, c->d_in_phi, c->d_in_chi,
-                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status, c->d_band, c->d_bs};
+                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status, c->d_band, c->d_bs, c->d_kd64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
@@ -294,18 +294,28 @@ __global__ void k_biortho(double2* phi, double2* chi, const int* __restrict__ np
   }
 }
 
-// Uploads host FP64 kernel data into the context's device tables (compute precision).
-template <typename T> cudaError_t put_tables(tc_ctx* c, const tc::KernelData& kd, cudaStream_t st) {
-  const std::vector<double>* src[] = {&kd.tabV, &kd.tabU, &kd.hartV, &kd.hartU, &kd.hartUs};
+// y = (T)(x + a dx) elementwise (FP64 arithmetic, one rounding to the compute precision)
+template <typename T>
+__global__ void k_displace(const double* __restrict__ x, const double* __restrict__ dx, double a, T* __restrict__ y,
+                           size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (T)(x[i] + a * dx[i]);
+}
+
+// The context's kernel tables set to K + a dK_m on the device (m < 0: K), from the FP64 copies of K and
+// of the four derivatives that tc_energy_grad keeps in d_kd64 (set m = 0 .. 3 after the base, set -1).
+template <typename T> cudaError_t displace_tables(tc_ctx* c, int m, double a, cudaStream_t st) {
   void* dst[] = {c->d_tabV, c->d_tabU, c->d_hartV, c->d_hartU, c->d_hartUs};
+  size_t set = 0;
+  for (int i = 0; i < 5; ++i) set += c->kd64_len[i];
+  size_t off = 0;
   for (int i = 0; i < 5; ++i) {
-    std::vector<T> h(src[i]->size());
-    for (size_t e = 0; e < h.size(); ++e) h[e] = (T)(*src[i])[e];
-    // pageable source: the call returns once the data is staged, so h may go out of scope
-    const cudaError_t r = cudaMemcpyAsync(dst[i], h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st);
-    if (r != cudaSuccess) return r;
+    const double* x = c->d_kd64 + off;
+    const double* dx = m < 0 ? x : c->d_kd64 + (size_t)(m + 1) * set + off;
+    k_displace<T><<<2 * 152, 256, 0, st>>>(x, dx, m < 0 ? 0.0 : a, static_cast<T*>(dst[i]), c->kd64_len[i]);
+    off += c->kd64_len[i];
   }
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -874,9 +884,37 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
         return fail(c, TC_ERR_OOM, "derivative tables: host allocation failed");
       }
     }
+    if (!c->d_kd64) {
+      // K and its four derivatives once on the device in FP64; each pass forms K + a dK there
+      const std::vector<double>* base_t[5] = {&S.tabV, &S.tabU, &S.hartV, &S.hartU, &S.hartUs};
+      size_t set = 0;
+      for (int i = 0; i < 5; ++i) set += (c->kd64_len[i] = base_t[i]->size());
+      if ((e = cudaMalloc((void**)&c->d_kd64, 5 * set * sizeof(double))) != cudaSuccess) {
+        c->d_kd64 = nullptr;
+        return cuda_fail(c, e, "derivative tables");
+      }
+      for (int m = -1; m < 4 && e == cudaSuccess; ++m) {
+        const tc::KernelData* kd = m < 0 ? nullptr : &c->dkd[m];
+        const std::vector<double>* src[5] = {
+            m < 0 ? base_t[0] : &kd->tabV, m < 0 ? base_t[1] : &kd->tabU, m < 0 ? base_t[2] : &kd->hartV,
+            m < 0 ? base_t[3] : &kd->hartU, m < 0 ? base_t[4] : &kd->hartUs};
+        size_t off = (size_t)(m + 1) * set;
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+          if (src[i]->size() != c->kd64_len[i]) {
+            e = cudaErrorInvalidValue;
+            break;
+          }
+          e = cudaMemcpy(c->d_kd64 + off, src[i]->data(), src[i]->size() * sizeof(double), cudaMemcpyHostToDevice);
+          off += src[i]->size();
+        }
+      }
+      if (e != cudaSuccess) {
+        cudaFree(c->d_kd64);
+        c->d_kd64 = nullptr;
+        return cuda_fail(c, e, "derivative tables");
+      }
+    }
     const double corr0[2] = {S.corr_c[0], S.corr_c[1]}, amp0[2] = {S.amp[0], S.amp[1]};
-    tc::KernelData base;
-    base.tabV = S.tabV; base.tabU = S.tabU; base.hartV = S.hartV; base.hartU = S.hartU; base.hartUs = S.hartUs;
     double twE[NT];
     term_weights(c, twE, 0.5, 1.0 / 3.0);
     r = TC_OK;
@@ -889,17 +927,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
       double Epm[2] = {0.0, 0.0};
       for (int sg = 0; sg < 2 && r == TC_OK; ++sg) {
         const double a = sg == 0 ? t : -t;
-        tc::KernelData kd;
-        auto axpy = [&](const std::vector<double>& x, const std::vector<double>& dx, std::vector<double>& y) {
-          y.resize(x.size());
-          for (size_t i = 0; i < x.size(); ++i) y[i] = x[i] + a * dx[i];
-        };
-        axpy(base.tabV, dk.tabV, kd.tabV);
-        axpy(base.tabU, dk.tabU, kd.tabU);
-        axpy(base.hartV, dk.hartV, kd.hartV);
-        axpy(base.hartU, dk.hartU, kd.hartU);
-        axpy(base.hartUs, dk.hartUs, kd.hartUs);
-        e = c->prec == TC_FP64 ? put_tables<double>(c, kd, st) : put_tables<float>(c, kd, st);
+        e = c->prec == TC_FP64 ? displace_tables<double>(c, m, a, st) : displace_tables<float>(c, m, a, st);
         if (e != cudaSuccess) { r = cuda_fail(c, e, "displaced tables"); break; }
         for (int s = 0; s < 2; ++s) {
           S.corr_c[s] = corr0[s] + a * dk.corr_c[s];
@@ -915,7 +943,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
       S.corr_c[s] = corr0[s];
       S.amp[s] = amp0[s];
     }
-    e = c->prec == TC_FP64 ? put_tables<double>(c, base, st) : put_tables<float>(c, base, st);
+    e = c->prec == TC_FP64 ? displace_tables<double>(c, -1, 0.0, st) : displace_tables<float>(c, -1, 0.0, st);
     if (r != TC_OK) return r;
     if (e != cudaSuccess) return cuda_fail(c, e, "table restore");
   }

@@ -33,6 +33,10 @@ struct tc_ctx {
   void* d_hartV = nullptr;         // [2][N] T
   void* d_hartU = nullptr;         // [N] T
   void* d_hartUs = nullptr;        // [2][N] T
+  // tc_energy_grad: the base kernel data and its four derivatives (FP64, device, built by the first
+  // call) and the element counts of the five tables
+  double* d_kd64 = nullptr;
+  size_t kd64_len[5] = {0, 0, 0, 0, 0};
   double* d_occ = nullptr;         // [Nk][nb]
   double* h_occ = nullptr;         // pinned [Nk][nb]
   // real-space orbitals
