@@ -35,9 +35,9 @@ CHAIN_KERNEL = "k_pair_chain_pr<float,24,17>"   # the bench cell's pair densitie
 SUPPORT = 17
 # DRAM bytes (read + write) of one k_pair_chain_pr<float,24,17> launch on the 4x4x4 workload, by the
 # partner-chunk count the autotuner chose, from one 1-pass capture of the timed apply (the 3 warm-ups and
-# the autotuner's 18 applies skipped); profiles/k_pair_chain_pr_f32_si_k444_dram.md.  Reported only for a
+# the autotuner's 18 applies skipped); profiles/dram_pruned_kernels_f32_si_k444.md.  Reported only for a
 # captured chunk count; cleared whenever the kernel changes.
-CHAIN_TRAFFIC = {5: 11.546e9 + 31.753e9}
+CHAIN_TRAFFIC = {5: 10.785e9 + 27.155e9}
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
 
@@ -419,6 +419,34 @@ def measure_batch(dev):
             "lanes_tuned_ms": {str(k): v for k, v in tune.items()}}
 
 
+def run_profile_cell(args):
+    """FP32 applies (warm-up + steps) of one HEG cell with plane-wave orbitals, nothing printed: the 48^3
+    HEG (heg_114) or cell I of the 256-cell batch recipe (batch:I), for ncu captures."""
+    import torch
+    from paper_2302_07420_gb300 import synth
+    from paper_2302_07420_gb300.operator import Context
+    name = args.profile_cell
+    if name == "heg_114":
+        c = synth.WORKLOADS["heg_114"]()
+    elif name.startswith("batch:"):
+        c = synth.heg_batch(256)[int(name.split(":", 1)[1])]
+    else:
+        raise SystemExit("--profile-cell: heg_114 or batch:I")
+    ctx = Context(c["lattice"], c["kmesh"], c["ecut"], c["fft"], c["nbands"], c["nocc"], c["A"], c["C"],
+                  precision="fp32")
+    npw, miller = ctx.layout()
+    kpg = kpg_list(c["lattice"], c["kmesh"], miller, npw)
+    d = torch.from_numpy(synth.heg_kpoint_orbitals(kpg, [miller[k, : npw[k]] for k in range(ctx.nk)], ctx.npw_max,
+                                                   c["nocc"])).cuda()
+    occ = synth.occupations(ctx.nk, c["nbands"], c["nocc"])
+    r, l_ = ctx.apply(d, d, occ)
+    for _ in range(args.warmup - 1 + args.steps):
+        ctx.apply(d, d, occ, r, l_)
+    torch.cuda.synchronize()
+    ctx.close()
+    return 0
+
+
 def run_batch(args):
     """The 256-cell HEG batch (boxes 16^3-32^3, 1-8 k-points), FP32, one CUDA-graph launch per step."""
     import torch
@@ -508,10 +536,15 @@ def main():
                     help="with --profile-run: symmetric model orbitals and the T_d + time-reversal reduction")
     ap.add_argument("--profile-davidson", action="store_true",
                     help="FP32 Davidson steps only (warm-up + steps), no JSON line: the ncu capture command")
+    ap.add_argument("--profile-cell", default=None,
+                    help="FP32 applies only (warm-up + steps), no JSON line, of one HEG cell: heg_114 (the 48^3 HEG) "
+                         "or batch:I (cell I of the 256-cell batch recipe): the ncu capture command")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_cell:
+        return run_profile_cell(args)
     if args.workload == "heg_batch":
         return run_batch(args)
 

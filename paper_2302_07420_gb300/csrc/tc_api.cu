@@ -924,6 +924,17 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
       const double theta = m < 2 ? S.prm.A[m] : S.prm.C[m - 2];
       const double t = 0.5 * std::max(std::fabs(theta), 0.1);
       const tc::KernelData& dk = c->dkd[m];
+      // the work of the pair stages that reads only the antiparallel u table ([delta][1][N] of tabU) is
+      // the same in both passes when dK has no antiparallel part, and cancels in the difference: skip it
+      bool ap_zero = true;
+      const size_t nn = (size_t)S.N;
+      for (size_t o = nn; ap_zero && o < dk.tabU.size(); o += 2 * nn)
+        for (size_t i = 0; i < nn; ++i)
+          if (dk.tabU[o + i] != 0.0) {
+            ap_zero = false;
+            break;
+          }
+      c->skip_ap = ap_zero ? 1 : 0;
       double Epm[2] = {0.0, 0.0};
       for (int sg = 0; sg < 2 && r == TC_OK; ++sg) {
         const double a = sg == 0 ? t : -t;
@@ -939,6 +950,7 @@ tc_status tc_energy_grad(tc_ctx* c, const void* phi, const void* chi, const doub
       if (r == TC_OK) dst[m % 2] = (Epm[0] - Epm[1]) / (2.0 * t);
     }
     // restore the kernel data of the context (also after a failure)
+    c->skip_ap = 0;
     for (int s = 0; s < 2; ++s) {
       S.corr_c[s] = corr0[s];
       S.amp[s] = amp0[s];

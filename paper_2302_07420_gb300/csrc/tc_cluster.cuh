@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(ClCfg<T, N, 0>::threads, ClCfg<T, N, 0>::MINB)
   const bool need_y = tw[T3B3] != T(0) || tw[T2BX2] != T(0);
   const bool need_pp = need_w || need_z || tw[T3B6] != T(0);
   const bool need_F = need_y || tw[T3B5] != T(0) || tw[T3B6] != T(0);
-  const bool need_ap = tw[T3B6] != T(0);
+  const bool need_ap = tw[T3B6] != T(0) && !P.no_ap;
   const T t3b5 = tw[T3B5], t3b6 = tw[T3B6], t2ax = tw[T2AX];
   for (int r = rank * blockDim.x + threadIdx.x; r < (int)NN; r += CL * blockDim.x) {
     acc[r] = cplx<T>{0, 0};
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(ClCfg<T, N, 2>::threads, ClCfg<T, N, 2>::MINB)
     const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
     const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
     for (int sp = 0; sp < 2; ++sp) {
-      if (sp == 1 && (!ap_here || P.h3_only)) continue;
+      if (sp == 1 && (!ap_here || P.h3_only || P.no_ap)) continue;
       const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
       const T* U21 = P.tabU + ((size_t)id21 * 2 + sp) * NN;
       const T* U12 = P.tabU + ((size_t)id12 * 2 + sp) * NN;

@@ -84,6 +84,9 @@ struct tc_ctx {
   // cluster-distributed pair kernels that can be scheduled on this device (bit 0 chain, 1 3b4,
   // 2 occupied pairs; tc_cluster.cuh), set by prepare_kernels
   int cluster_ok = 0;
+  // set by tc_energy_grad for its passes along a derivative that is zero in the antiparallel kernel
+  // table: the pair stages skip the work that reads only that table (it cancels in the difference)
+  int skip_ap = 0;
   // compiled plans of the box: support length of the one-CTA pruned kernels (0: none), of the
   // cluster kernels (0: none) and the cluster widths of the chain, 3b4 and occupied-pair kernels
   int plan_prune_L = 0, plan_cl_L = 0;

@@ -79,6 +79,7 @@ template <typename T> struct Params {
                          // acc, w, Y and cs are indexed by j - j0
   int i2_0, nq2;         // occupied-pair stage: q2 items i2_0 .. i2_0 + nq2 - 1 (item = k no + mu)
   int h3_only;           // occupied-pair stage: the two h3 kinds only (parallel spins, no h6)
+  int no_ap;             // pair stages without the work that reads only the antiparallel kernel table
   int band;              // outputs at band points: no SCF-mesh 3b6 corrections in k_finalize
   int nkb;               // band points (band contexts)
   const double* bandc;   // [nkb][4]: W (3), Gamma_b

@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_occ_pairs(Params<T> P) {
       const bool ap_here = P.sym || cyc == 0 || 2 * cyc < M || (2 * cyc == M && i2 < i1);
       const T ap_w = (P.sym || cyc == 0) ? T(1) : T(2);
       for (int sp = 0; sp < 2; ++sp) {
-        if (sp == 1 && (!ap_here || P.h3_only)) continue;
+        if (sp == 1 && (!ap_here || P.h3_only || P.no_ap)) continue;
         const T w12 = (sp == 1 ? ap_w : T(1)) * (f1 * f2);
         for (int d = 0; d < 3; ++d) {
           const PComp<T> q21 = pcomp_setup<T>(P, d21, d), q12 = pcomp_setup<T>(P, d12, d);
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(Cfg<N>::threads, 1) k_pair_chain(Params<T> P) 
   const bool need_y = tw[T3B3] != T(0) || tw[T2BX2] != T(0);
   const bool need_pp = need_w || need_z || tw[T3B6] != T(0);
   const bool need_F = need_y || tw[T3B5] != T(0) || tw[T3B6] != T(0);
-  const bool need_ap = tw[T3B6] != T(0);
+  const bool need_ap = tw[T3B6] != T(0) && !P.no_ap;
   const T t3b5 = tw[T3B5], t3b6 = tw[T3B6];
   for (int r = threadIdx.x; r < (int)NN; r += blockDim.x) {
     acc[r] = cplx<T>{0, 0};

@@ -81,6 +81,7 @@ template <typename T, int N> static Params<T> make_params(tc_ctx* ctx, const dou
   P.i2_0 = 0;
   P.nq2 = S.Nk * S.no;
   P.h3_only = 0;
+  P.no_ap = ctx->skip_ap;
   P.band = 0;
   P.nkb = S.nkb;
   P.bandc = ctx->d_band;
