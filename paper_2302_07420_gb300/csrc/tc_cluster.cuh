@@ -13,7 +13,8 @@
 //     every CTA through distributed shared memory.
 //   * Every pass pair (and every axis-1 pass) ends with a cluster barrier (arrive.release /
 //     wait.acquire), which orders the shared-memory rows between CTAs and the global accumulator
-//     writes of the cluster.  Control flow that reaches a cluster barrier depends only on the
+//     writes of the cluster -- except the chain's per-component forward passes, which a
+//     cluster-barrier-closed inverse pass of the same CTA always follows.  Control flow that reaches a cluster barrier depends only on the
 //     launch parameters and the cluster's item, so every CTA of a cluster arrives at every barrier.
 // The arithmetic per pair is that of the pruned kernels, exact for the discrete operator whenever
 // the pair-density support fits L.
@@ -188,8 +189,11 @@ __device__ __forceinline__ void caxis1(cg::cluster_group& cluster, cplx<T>* cons
 
 // Forward transform, axes 3 and 2, of this CTA's work rows (axis 1 done) onto the support;
 // emit(r, c1, c2, c3, value) receives each output of the rows once, from the thread that owns the
-// compact pencil (r, c3) -- the same thread that reads it in cinv_23.
-template <typename T, int N, int L, int CL, typename Emit>
+// compact pencil (r, c3) -- the same thread that reads it in cinv_23.  It ends with a cluster barrier
+// (the next axis-1 pass may write into these rows from another CTA), or with a CTA barrier when
+// CSYNC is false: allowed where a cinv_23 of this CTA, which ends with a cluster barrier, comes
+// before any such pass.
+template <typename T, int N, int L, int CL, bool CSYNC = true, typename Emit>
 __device__ __forceinline__ void cfwd_32(cg::cluster_group& cluster, cplx<T>* B, int c1_0, int nrow, Emit emit) {
   using S = Sup<N, L>;
   using D = Dist<T, N, L, CL>;
@@ -212,7 +216,11 @@ __device__ __forceinline__ void cfwd_32(cg::cluster_group& cluster, cplx<T>* B, 
 #pragma unroll
     for (int c2 = 0; c2 < L; ++c2) emit(r, c1_0 + r, c2, c3, v[S::box(c2)]);
   }
-  cluster.sync();
+  if constexpr (CSYNC) {
+    cluster.sync();
+  } else {
+    __syncthreads();
+  }
 }
 
 // Fused pair chains, distributed (same work, accumulators and per-pair arithmetic as
@@ -404,8 +412,9 @@ __global__ void __launch_bounds__(ClCfg<T, N, 0>::threads, ClCfg<T, N, 0>::MINB)
             },
             fwd);
         if (!fwd) continue;
-        // C += -U_d FT[F] = -i p_d u FT[F]
-        cfwd_32<T, N, L, CL>(cluster, B, c1_0, nrow, [&](int r, int c1, int c2, int c3, cplx<T> v) {
+        // C += -U_d FT[F] = -i p_d u FT[F]; a cinv_23 always follows (the next component's or the
+        // final one: C is then nonzero), so a CTA barrier closes the pass
+        cfwd_32<T, N, L, CL, false>(cluster, B, c1_0, nrow, [&](int r, int c1, int c2, int c3, cplx<T> v) {
           const T k = pcomp_c<T, N, L>(qd, c1, c2, c3) * tab(sp, r, c1, c2, c3) * P.invN;
           const cplx<T> t = mul_si<T, -1>(k * v);
           const int s = D::cidx(r, c2, c3);
