@@ -30,10 +30,12 @@ namespace cg = cooperative_groups;
 // One kernel's cluster configuration: CTAs per cluster, which compact spectra sit in shared memory
 // (spec 1: all; 2: the chain's pair spectrum A only, its accumulator C in the scratch slice; 0: none,
 // the spectra in the item's scratch slice, each CTA touching its own rows only), the CTAs per SM its
-// launch bounds ask for, the threads per CTA (0: one axis-1 pencil per thread), and the elements per
-// load chunk of the chain's pointwise pass (its loads for a chunk are issued together).
+// launch bounds ask for, the threads per CTA (0: one axis-1 pencil per thread), the elements per
+// load chunk of the chain's pointwise pass (its loads for a chunk are issued together), and, for the
+// occupied-pair kernel, whether the item's h6 part accumulates in shared memory (h6 = 1: by axis-1
+// pencil, each element owned by one thread, written to the item's scratch slot once at the end).
 struct ClChoice {
-  int cl, spec, minb, thr, ch;
+  int cl, spec, minb, thr, ch, h6 = 0;
 };
 
 // Cluster plan for box size N: the support length L of the distributed kernels (0: none built; the
@@ -58,9 +60,9 @@ template <typename T, int N> struct ClPlan {
   }
   static constexpr int nspec(int kind) { return kind == 1 ? 1 : 2; }
   // bytes of the row slices: work rows (and, for kind 2, B1 by pencil), then the spectra on chip
-  static constexpr size_t bytes(int kind, int cl, int spec) {
+  static constexpr size_t bytes(int kind, int cl, int spec, int h6 = 0) {
     const size_t b = (size_t)rows(cl) * N * P * z;
-    const size_t base = kind == 2 ? (size_t)N * pens(cl) * z + b : b;
+    const size_t base = kind == 2 ? (size_t)(h6 ? 2 : 1) * N * pens(cl) * z + b : b;
     const int on_chip = spec == 1 ? nspec(kind) : (spec == 2 ? 1 : 0);
     return base + (size_t)on_chip * rows(cl) * L * L * z;
   }
@@ -76,7 +78,7 @@ template <typename T, int N> struct ClPlan {
     if (sizeof(T) == 8) return choice64(kind);
     switch (N) {
       case 24: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : ClChoice{2, 1, 1, 0, 1};
-      case 25: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
+      case 25: return kind == 0 ? ClChoice{2, 1, 1, 0, 4} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1, 1});
       case 27: return kind == 0 ? ClChoice{2, 1, 1, 0, 2} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
       case 30: return kind == 0 ? ClChoice{2, 2, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{2, 0, 1, 0, 1});
       case 32: return kind == 0 ? ClChoice{2, 2, 1, 0, 1} : (kind == 1 ? ClChoice{2, 1, 1, 0, 1} : ClChoice{3, 0, 1, 0, 1});
@@ -99,7 +101,8 @@ template <typename T, int N, int KIND> struct ClCfg {
   // pencil takes 4 N registers); the passes loop over their pencils, so any count is correct
   static constexpr int want = PL::choice(KIND).thr > 0 ? PL::choice(KIND).thr : PL::need(CL);
   static constexpr int threads = (sizeof(T) == 8 && want > 256) ? 256 : want;
-  static constexpr size_t bytes = PL::bytes(KIND, CL, PL::choice(KIND).spec);
+  static constexpr bool H6S = KIND == 2 && PL::choice(KIND).h6 != 0;   // h6 part in shared memory
+  static constexpr size_t bytes = PL::bytes(KIND, CL, PL::choice(KIND).spec, H6S ? 1 : 0);
   // kernel-table rows of the current Delta (3 for the chain, 1 for 3b4) when they fit as well
   static constexpr size_t tab_bytes = (size_t)(KIND == 0 ? 3 : 1) * PL::rows(CL) * L * L * sizeof(T);
   static constexpr bool tab = (KIND == 0 ? SPEC : (KIND == 1 && SPEC_A)) &&
@@ -583,7 +586,8 @@ __global__ void __launch_bounds__(ClCfg<T, N, 2>::threads, ClCfg<T, N, 2>::MINB)
   cplx<T>* FAB = slice + 2 * (size_t)G::vol;
   cplx<T>* H6 = slice + 4 * (size_t)G::vol;
   cplx<T>* R1 = reinterpret_cast<cplx<T>*>(smraw);
-  cplx<T>* W = R1 + (size_t)N * D::PEN;
+  cplx<T>* H6s = R1 + (size_t)N * D::PEN;                       // used when SM::H6S
+  cplx<T>* W = SM::H6S ? H6s + (size_t)N * D::PEN : H6s;
   cplx<T>* A1;
   cplx<T>* A2;
   if constexpr (SM::SPEC) {
@@ -604,8 +608,11 @@ __global__ void __launch_bounds__(ClCfg<T, N, 2>::threads, ClCfg<T, N, 2>::MINB)
   const cplx<T>* ket2 = SD.ket + (size_t)q2 * NN;
   const int tid = rank * blockDim.x + threadIdx.x, nthr = CL * blockDim.x;
   for (int r = tid; r < S::cvol; r += nthr) FAB[r] = cplx<T>{0, 0};
+  if constexpr (SM::H6S) {
+    for (int r = threadIdx.x; r < N * D::PEN; r += blockDim.x) H6s[r] = cplx<T>{0, 0};
+  }
   for (int r = tid; r < (int)NN; r += nthr) {
-    H6[r] = cplx<T>{0, 0};
+    if constexpr (!SM::H6S) H6[r] = cplx<T>{0, 0};
     for (int d = 0; d < 3; ++d) {
       h3a4[d * NN + r] = cplx<T>{0, 0};
       h3b[d * NN + r] = cplx<T>{0, 0};
@@ -709,7 +716,12 @@ __global__ void __launch_bounds__(ClCfg<T, N, 2>::threads, ClCfg<T, N, 2>::MINB)
                   if (c0 + u >= N) continue;
                   const int g = G::gidx(c0 + u, a2, a3);
                   const cplx<T> b2 = v[c0 + u];
-                  red_add_v(&H6[g], w12 * (lb1[u] * b2));
+                  if constexpr (SM::H6S) {
+                    cplx<T>& h = H6s[(c0 + u) * D::PEN + t];
+                    h = h + w12 * (lb1[u] * b2);
+                  } else {
+                    red_add_v(&H6[g], w12 * (lb1[u] * b2));
+                  }
                   if (sp == 0) {
                     red_add_v(&h3a4[d * NN + g], f1 * (b2 * lk[u]));
                     red_add_v(&h3b[d * NN + g], f1 * mulc(lb1[u], lr[u]));
@@ -734,11 +746,26 @@ __global__ void __launch_bounds__(ClCfg<T, N, 2>::threads, ClCfg<T, N, 2>::MINB)
     });
     caxis1<T, N, L, CL, true>(
         cluster, rb, rank, [&](int, int, int) { return cplx<T>{0, 0}; },
-        [&](int, int a2, int a3, cplx<T>(&v)[N]) {
+        [&](int t, int a2, int a3, cplx<T>(&v)[N]) {
 #pragma unroll
-          for (int i = 0; i < N; ++i) red_add_v(&H6[G::gidx(i, a2, a3)], pref * (v[i] + cF0));
+          for (int i = 0; i < N; ++i) {
+            if constexpr (SM::H6S) {
+              H6s[i * D::PEN + t] = H6s[i * D::PEN + t] + pref * (v[i] + cF0);
+            } else {
+              red_add_v(&H6[G::gidx(i, a2, a3)], pref * (v[i] + cF0));
+            }
+          }
         },
         false);
+  }
+  if constexpr (SM::H6S) {
+    // the item's h6 part: this CTA's pencils, by the threads that accumulated them
+    const int p0 = rank * D::PEN;
+    const int p1 = (p0 + D::PEN < N * N) ? p0 + D::PEN : N * N;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const int a2 = p / N, a3 = p % N, t = p - p0;
+      for (int i = 0; i < N; ++i) H6[G::gidx(i, a2, a3)] = H6s[i * D::PEN + t];
+    }
   }
   cluster.sync();
 }
