@@ -40,6 +40,10 @@
  * tc_autotune, tc_davidson_step, tc_apply_batch and tc_apply_noalloc return
  * TC_ERR_CUDA (TC_FAULT=launch) or TC_ERR_TIMEOUT (TC_FAULT=timeout) before
  * any kernel launch, with the outputs untouched and the context usable.
+ * TC_FAULT=nocluster makes tc_init treat every thread-block-cluster pair
+ * kernel as one the device cannot hold (as cudaOccupancyMaxActiveClusters
+ * reporting 0 would): its contexts run the one-CTA kernels with full
+ * transforms instead (tc_pair_kernels reports it; results equal to rounding).
  * TC_ERR_TIMEOUT is otherwise not returned: no kernel of this library waits
  * on a flag or on another kernel.
  * Threads: a context is not thread-safe; distinct contexts are independent.

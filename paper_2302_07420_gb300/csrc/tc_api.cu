@@ -615,6 +615,7 @@ int injected_fault(const char* site) {
   if (at == "alloc" && f == "alloc") return TC_ERR_OOM;
   if (at == "launch" && f == "launch") return TC_ERR_CUDA;
   if (at == "launch" && f == "timeout") return TC_ERR_TIMEOUT;
+  if (at == "cluster" && f == "nocluster") return TC_ERR_UNSUPPORTED;
   return TC_OK;
 }
 

@@ -125,8 +125,10 @@ static cudaError_t launch_cluster(void (*kern)(Args...), dim3 grid, int threads,
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// Sets the kernel's shared-memory size and reports whether one cluster of it fits the device.
+// Sets the kernel's shared-memory size and reports whether one cluster of it fits the device (never
+// under the host fault switch TC_FAULT=nocluster).
 template <typename K> static bool cluster_fits(tc_ctx*, K kern, int cl, int threads, size_t smem) {
+  if (injected_fault("cluster") != TC_OK) return false;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return false;

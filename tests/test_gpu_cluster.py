@@ -8,7 +8,8 @@ box at 48^3.  Beyond the compiled support the one-CTA
 kernels with full transforms run (kind 0).  Cases: spans
 from 2 to 11 on triclinic and silicon-like cells, 1-2 k-points, partial occupations; every term
 separately in FP64 (1e-11) and the totals in FP64 and FP32 (1e-5); partner chunks and the one-sided
-energy; a band point off the mesh; the symmetry-reduced occupied-pair stage.
+energy; a band point off the mesh; the symmetry-reduced occupied-pair stage; the one-CTA fallback
+when no cluster fits the device (forced by the host fault switch TC_FAULT=nocluster).
 """
 import numpy as np
 import pytest
@@ -141,6 +142,28 @@ def test_cluster_plan_is_reported():
     finally:
         ctx.close()
     assert info == {k: (0, 27, 1) for k in ("pair_chain", "pair_3b4", "occ_pairs")}, info
+
+
+@pytest.mark.parametrize("name", ["c25_span8", "c32_span8", "c48_span4"])
+def test_one_cta_fallback_when_no_cluster_fits(name, monkeypatch):
+    """TC_FAULT=nocluster (a device that cannot hold the clusters): the contexts take the one-CTA kernels
+    with full transforms, reported by tc_pair_kernels, and compute the same operator."""
+    p, S, c_phi, c_chi, occ, ref_r, ref_l = _ref(name)
+    tr, tl = OP.total(ref_r), OP.total(ref_l)
+    scale = max(np.abs(tr).max(), np.abs(tl).max())
+    monkeypatch.setenv("TC_FAULT", "nocluster")
+    for prec in ("fp64", "fp32"):
+        ctx = _ctx(p, precision=prec)
+        try:
+            info = ctx.pair_kernels()
+            out_r, out_l = ctx.apply(_dev(c_phi), _dev(c_chi), occ)
+            torch.cuda.synchronize()
+        finally:
+            ctx.close()
+        assert info == {k: (0, p["fft"][0], 1) for k in ("pair_chain", "pair_3b4", "occ_pairs")}, info
+        er = np.abs(out_r.cpu().numpy() - tr).max() / scale
+        el = np.abs(out_l.cpu().numpy() - tl).max() / scale
+        assert er < TOL[prec] and el < TOL[prec], (prec, er, el)
 
 
 def test_cluster_chunked_and_one_sided_energy():
