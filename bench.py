@@ -33,11 +33,12 @@ HBM_NOMINAL_GBPS = 7900.0
 FFTS_PER_PAIR_CHAIN = 14   # pair chain: rho, 3 pp inverse, 3 pp forward, 3 ap inverse, 3 ap forward, final (with V)
 CHAIN_KERNEL = "k_pair_chain_pr<float,24,17>"   # the bench cell's pair densities fit the 17-index support
 SUPPORT = 17
-# DRAM bytes (read + write) of one k_pair_chain_pr<float,24,17> launch on the 4x4x4 workload, by the
-# partner-chunk count the autotuner chose, from one 1-pass capture of the timed apply (the 3 warm-ups and
+# DRAM bytes (read + write) per k_pair_chain_pr<float,24,17> launch on the 4x4x4 workload, by the
+# partner-chunk count the autotuner chose and whether the two-sided apply is mirrored (two launches,
+# right then left: the mean of the two), from one 1-pass capture of the timed apply (the 3 warm-ups and
 # the autotuner's 18 applies skipped); profiles/dram_pruned_kernels_f32_si_k444.md.  Reported only for a
-# captured chunk count; cleared whenever the kernel changes.
-CHAIN_TRAFFIC = {5: 10.785e9 + 27.155e9}
+# captured configuration; cleared whenever the kernel changes.
+CHAIN_TRAFFIC = {(5, False): 10.788e9 + 27.166e9}
 WORKLOAD_DESC = ("si_k444: FCC a=10.26 bohr, 4x4x4 Gamma-centred k mesh, ecut 7.5 Ha, 24^3 box, "
                  "4 occupied bands, right+left operator")
 
@@ -624,20 +625,26 @@ def main():
     t = max_over_ranks(ms / 1e3, dist, dev)
     value = job_value(world, npairs, args.steps, t)
 
-    # dominant kernel (fused pair chains): algorithmic FFT flops / live per-launch time
+    # dominant kernel (fused pair chains): algorithmic FFT flops / live per-launch time.  A mirrored
+    # two-sided apply runs it twice (right side, then the left side with the reflected spectra): the
+    # flops per launch are then those of half the pair chains, the time the mean of the two launches
     pc_ms, pc_launch = stages["pair_chain"]
+    lpa = max(pc_launch, 1) / args.steps            # chain launches per apply
+    mirrored = ctx.pair_mirror()[0]
     n = p["fft"][0]
     N = n ** 3
     fft_flop = 5.0 * N * math.log2(N)
     chain_pairs = 2 * (ctx.nk * p["nbands"]) * (ctx.nk * p["nocc"])
-    flop_per_launch = chain_pairs * FFTS_PER_PAIR_CHAIN * fft_flop
-    achieved = flop_per_launch / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e12
+    flop_per_apply = chain_pairs * FFTS_PER_PAIR_CHAIN * fft_flop
+    flop_per_launch = flop_per_apply / lpa
+    ms_per_launch = pc_ms / max(pc_launch, 1)
+    achieved = flop_per_launch / (ms_per_launch / 1e3) / 1e12
     launches = sum(v[1] for v in stages.values())
     # HBM view of the same launch: measured DRAM bytes / live launch time, against the measured copy peak
-    traffic = CHAIN_TRAFFIC.get(so_sc[1]) if args.workload == "si_k444" else None
+    traffic = CHAIN_TRAFFIC.get((so_sc[1], mirrored)) if args.workload == "si_k444" else None
     hbm = None
     if traffic is not None:
-        gbps = traffic / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9
+        gbps = traffic / (ms_per_launch / 1e3) / 1e9
         hbm = {"achieved": gbps, "peak": hbm_peak_gbps(), "unit": "GB/s", "frac": gbps / hbm_peak_gbps(),
                "nominal_frac": gbps / HBM_NOMINAL_GBPS,
                "what": "ncu DRAM read+write bytes of one launch / its live CUDA-event time (of measured copy peak; "
@@ -648,10 +655,14 @@ def main():
     occ_executed = (ctx.nk * p["nocc"]) ** 2
     executed = chain_pairs + occ_executed
     pencils_pruned = SUPPORT * SUPPORT + SUPPORT * n + n * n
-    executed_flop = chain_pairs * FFTS_PER_PAIR_CHAIN * pencils_pruned * 5.0 * n * math.log2(n)
+    # mirrored: the left pair chains whose output band is a partner take the right side's pair and
+    # antiparallel spectra and run 7 of their 14 transforms (all of them here: nbands = nocc, f = 1)
+    left_mirrored = (ctx.nk * p["nocc"]) ** 2 if mirrored else 0
+    executed_ffts = chain_pairs * FFTS_PER_PAIR_CHAIN - left_mirrored * 7
+    executed_flop = executed_ffts * pencils_pruned * 5.0 * n * math.log2(n) / lpa
     # FFT-pass-equivalent bytes (each n^3 complex64 FFT reads and writes its volume once) per second: a
     # labelled "effective" rate for comparison with unfused FFT pipelines, not DRAM traffic
-    eff_gbps = chain_pairs * FFTS_PER_PAIR_CHAIN * 2 * N * 8 / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e9
+    eff_gbps = chain_pairs * FFTS_PER_PAIR_CHAIN * 2 * N * 8 / (pc_ms / 1e3 / args.steps) / 1e9
     # measured FMA throughput of the FP32 and FP64 pipes (tc_alu_peak), beside the derived FP32 peak
     peak32 = alu_peak("fp32", 50.0)
     peak64 = alu_peak("fp64", 50.0)
@@ -671,7 +682,7 @@ def main():
     ms64 = e0.elapsed_time(e1) / args.fp64_steps
     pc64_ms, pc64_launch = ctx64.stage_times()["pair_chain"]
     ctx64.profile(False)
-    achieved64 = flop_per_launch / (pc64_ms / 1e3 / max(pc64_launch, 1)) / 1e12
+    achieved64 = flop_per_apply / (pc64_ms / 1e3 / args.fp64_steps) / 1e12
     ref_scale = max(float(r64.abs().max()), float(l64.abs().max()))
     err32 = max(float((out_r - r64).abs().max()), float((out_l - l64).abs().max())) / ref_scale
     # total energy per cell (Eqs. EtotTC / EtotBiTC): FP32 path against the FP64 path, per electron
@@ -711,7 +722,7 @@ def main():
     if not args.no_extras and args.workload == "si_k444":
         extras = measure_extras(p, c_phi, c_chi, occ, d_phi, d_chi, dev)
         extras["cufft_comparison"] = cufft_comparison(n, chain_pairs * FFTS_PER_PAIR_CHAIN,
-                                                      pc_ms / max(pc_launch, 1), dev)
+                                                      pc_ms / args.steps, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -732,9 +743,11 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": CHAIN_KERNEL,
                          "flop_convention": "algorithmic: 14 full n^3 FFTs of 5 N log2 N per pair chain; the pruned "
-                                            "transforms execute fewer (executed.pair_chain_executed_flop_per_launch)",
+                                            "transforms and the mirrored left chains execute fewer "
+                                            "(executed.pair_chain_executed_flop_per_launch)",
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                         "flop_per_launch": flop_per_launch, "ms_per_launch": pc_ms / max(pc_launch, 1),
+                         "flop_per_launch": flop_per_launch, "ms_per_launch": ms_per_launch,
+                         "launches_per_apply": lpa, "mirrored": mirrored,
                          "measured_alu_peak": {"fp32_tflops": peak32, "fp64_tflops": peak64,
                                                "frac_fp32": achieved / peak32, "source": "tc_alu_peak (FMA chains)"},
                          "effective_gbs": eff_gbps, "hbm": hbm},
@@ -757,7 +770,8 @@ def main():
                          "pair_convolutions_per_step": executed, "pairs_per_s": executed * args.steps / t,
                          "represented_pair_convolutions_per_step": npairs,
                          "pair_chain_executed_flop_per_launch": executed_flop,
-                         "pair_chain_executed_tflops": executed_flop / (pc_ms / 1e3 / max(pc_launch, 1)) / 1e12,
+                         "pair_chain_executed_tflops": executed_flop / (ms_per_launch / 1e3) / 1e12,
+                         "pair_chain_executed_ffts_per_apply": executed_ffts,
                          "pruned_support": SUPPORT},
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,

@@ -291,6 +291,23 @@ tc_status tc_stage_times(const tc_ctx* ctx, double* ms, int* launches, int n);
  * tc_batch_cell), TC_ERR_ARG (null info). */
 tc_status tc_pair_kernels(const tc_ctx* ctx, int* info);
 
+/* tc_pair_mirror -- whether two-sided applies of this context mirror their pair chains.  The left
+ * operator (Eq. BITCSCFconj) of output q and partner j has the complex conjugate of the right pair
+ * density of output j and partner q, and the kernel momentum -(k_j - k_q + G); with u~ real and
+ * even (Appendix B) the left pair spectrum and the left antiparallel 3b6 spectrum of Alg. 12 are
+ * the conjugate reflections (G -> -G) of the right ones.  A mirrored two-sided apply runs the right
+ * pair chains first, storing those reflections for every pair whose output is itself a partner
+ * (band < nocc), and the left chains then take them instead of recomputing them (7 of the 14
+ * transforms of such a pair chain).  Exact up to rounding; used by TC_FP64 contexts whose pair
+ * chains run the pruned kernels (tc_pair_kernels kind 1) on the SCF mesh without crystal symmetry,
+ * with a buffer of (Nk nocc)^2 x 2 x support^3 complex FP64 values that tc_init allocates when it
+ * fits in a quarter of the free device memory (not for FP32 contexts, whose pair chains are bound
+ * by the loads that both sides keep; not for batch cells, band-point contexts or
+ * tc_apply_noalloc).  *active = 1 when such a buffer is held (one-sided launches do not use it),
+ * *bytes = its size (0 when inactive).  TC_FAULT=nomirror makes tc_init hold none, as if it did not
+ * fit.  Either pointer may be NULL.  Errors: TC_ERR_STATE (null context or a batch). */
+tc_status tc_pair_mirror(const tc_ctx* ctx, int* active, unsigned long long* bytes);
+
 /* tc_band_constants -- the constants of the divergence corrections at
  * band-structure k-points off the SCF mesh (Sec. 2.6.3 after Eq.
  * divcorr_2ax_scf: Eqs. divcorr_2ax_band and 3b6_div_band1 use the scalar,

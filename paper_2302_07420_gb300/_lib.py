@@ -22,7 +22,7 @@ EXPORTED = ("tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy",
             "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
             "tc_davidson_step", "tc_set_symmetry", "tc_symmetry_info", "tc_symmetrize_orbitals", "tc_autotune",
             "tc_alu_peak", "tc_band_constants", "tc_band_layout", "tc_init_band", "tc_apply_band",
-            "tc_pair_kernels")
+            "tc_pair_kernels", "tc_pair_mirror")
 TC_NSTAGES = 6
 STAGES = ("orbitals", "hartree", "occ_pairs", "pair_chain", "pair_3b4", "finalize")
 STATUS = {TC_ERR_ARG: "TC_ERR_ARG", TC_ERR_STATE: "TC_ERR_STATE", TC_ERR_OOM: "TC_ERR_OOM",
@@ -99,11 +99,12 @@ def load():
     lib.tc_band_layout.argtypes = [ctypes.POINTER(tc_params), dp, ip, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)]
     lib.tc_init_band.argtypes = [ctypes.POINTER(tc_params), ip, dp, ctypes.POINTER(vp)]
     lib.tc_apply_band.argtypes = [vp, vp, vp, dp, vp, vp, dp, vp, vp, vp]
+    lib.tc_pair_mirror.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_ulonglong)]
     for name in ("tc_init_band", "tc_apply_band", "tc_init", "tc_layout", "tc_setup_scalars", "tc_apply", "tc_energy", "tc_fft3d", "tc_destroy",
                  "tc_profile", "tc_stage_times", "tc_apply_noalloc", "tc_energy_grad",
             "tc_biorthonormalize", "tc_init_batch", "tc_batch_cell", "tc_apply_batch", "tc_batch_info",
             "tc_davidson_step", "tc_set_symmetry", "tc_symmetry_info", "tc_symmetrize_orbitals", "tc_autotune",
-            "tc_alu_peak", "tc_band_constants", "tc_band_layout"):
+            "tc_alu_peak", "tc_band_constants", "tc_band_layout", "tc_pair_mirror"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

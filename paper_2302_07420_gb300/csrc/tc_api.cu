@@ -96,7 +96,8 @@ template <typename T> void* upload_as(const std::vector<double>& v, cudaError_t&
 void free_all(tc_ctx* c) {
   void* ptrs[] = {c->d_box_index, c->d_kpg, c->d_delta_id, c->d_delta, c->d_tabV, c->d_tabU, c->d_hartV,
                   c->d_hartU, c->d_hartUs, c->d_occ, c->ws_owned ? c->d_ws : nullptr, c->d_in_phi, c->d_in_chi,
-                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status, c->d_band, c->d_bs, c->d_kd64};
+                  c->d_out_R, c->d_out_L, c->d_edot, c->d_npw, c->d_status, c->d_band, c->d_bs, c->d_kd64,
+                  c->d_mirror};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ev : c->ev)
@@ -616,7 +617,35 @@ int injected_fault(const char* site) {
   if (at == "launch" && f == "launch") return TC_ERR_CUDA;
   if (at == "launch" && f == "timeout") return TC_ERR_TIMEOUT;
   if (at == "cluster" && f == "nocluster") return TC_ERR_UNSUPPORTED;
+  if (at == "mirror" && f == "nomirror") return TC_ERR_OOM;
   return TC_OK;
+}
+
+// The reflection buffer of mirrored two-sided pair chains (tc_ctx::d_mirror): for FP64 contexts
+// whose pair chains run the pruned kernels on the SCF mesh, when it takes at most a quarter of the
+// free device memory; otherwise (or under TC_FAULT=nomirror, as if it did not fit) none.  (FP32 pair
+// chains are bound by the loads of their parallel-spin passes, which the mirror does not remove;
+// measured on the 4x4x4 silicon-like cell, the right launch's stores cost more than the left launch
+// saves.)
+static void alloc_mirror(tc_ctx* c) {
+  const Setup& S = c->S;
+  if (c->prec != TC_FP64) return;
+  if (S.nkb > 0 || c->plan_prune_L <= 0 || c->pair_support > c->plan_prune_L) return;
+  if (injected_fault("mirror") != TC_OK) return;
+  const size_t L = (size_t)c->plan_prune_L, M = (size_t)S.Nk * S.no;
+  const size_t bytes = M * M * 2 * L * L * L * c->esz;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (bytes > fr / 4) return;
+  if (cudaMalloc(&c->d_mirror, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_mirror = nullptr;
+    return;
+  }
+  c->mirror_bytes = bytes;
 }
 
 }  // namespace tc
@@ -627,6 +656,7 @@ tc_status tc_init(const tc_params* params, tc_ctx** out) {
   if (!params || !out) return TC_ERR_ARG;
   std::string err;
   const int r = tc::init_context(params, true, out, err);
+  if (r == TC_OK) tc::alloc_mirror(*out);
   g_init_err = err;
   return (tc_status)r;
 }
@@ -1177,6 +1207,13 @@ tc_status tc_pair_kernels(const tc_ctx* c, int* info) {
       o[0] = 0; o[1] = c->S.n; o[2] = 1;
     }
   }
+  return TC_OK;
+}
+
+tc_status tc_pair_mirror(const tc_ctx* c, int* active, unsigned long long* bytes) {
+  if (!c || c->batch) return TC_ERR_STATE;
+  if (active) *active = c->d_mirror ? 1 : 0;
+  if (bytes) *bytes = (unsigned long long)c->mirror_bytes;
   return TC_OK;
 }
 

@@ -81,6 +81,12 @@ struct tc_ctx {
   // box indices per axis that a pair-density spectrum can occupy (tc::pair_support_len); the pair
   // chains use their pruned transforms when it fits the compiled support length (large: never)
   int pair_support = 1 << 30;
+  // two-sided applies with the pruned pair kernels: the left pair chains take their pair spectra
+  // and antiparallel 3b6 spectra from the right ones (k_pair_chain_pr, mirror); this buffer holds
+  // them ([Nk no][Nk no][2][L^3] in the compute precision), allocated by tc_init when it fits in a
+  // quarter of the free device memory, else null (each side computes its own)
+  void* d_mirror = nullptr;
+  size_t mirror_bytes = 0;
   // cluster-distributed pair kernels that can be scheduled on this device (bit 0 chain, 1 3b4,
   // 2 occupied pairs; tc_cluster.cuh), set by prepare_kernels
   int cluster_ok = 0;

@@ -84,6 +84,12 @@ template <typename T> struct Params {
   int nkb;               // band points (band contexts)
   const double* bandc;   // [nkb][4]: W (3), Gamma_b
   double2* bs;           // [2][nkb][no][nb][13] band correction scalars (tc_band.cuh)
+  // pair chains of a two-sided apply as two launches, right side first (k_pair_chain_pr): side0 is
+  // the side of blockIdx.y = 0; mirror = 1 writes, for every occupied output j, the conjugate
+  // reflections of each pair spectrum and antiparallel 3b6 spectrum into mir, mirror = 2 reads them
+  // as the left side's own (see k_pair_chain_pr); mirror = 0: each side computes its own
+  int side0, mirror;
+  cplx<T>* mir;          // [Nk no (left output)][Nk no (partner)][2][L^3] compact spectra
   SideArgs<T> side[2];
 };
 

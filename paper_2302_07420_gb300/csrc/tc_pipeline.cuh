@@ -460,9 +460,21 @@ int run_pipeline(tc_ctx* ctx, const double2* cphi, const double2* cchi, double2*
     Params<T> Pc = P;
     Pc.nsmem = smem_vols<T, N>(3);
     if constexpr (LP < N) {
-      if (pruned)
+      // two-sided FP64: the right side first, writing the reflections the left side then reads
+      const bool mirror = sizeof(T) == 8 && pruned && nsides == 2 && ctx->d_mirror && !P.sym && !band;
+      if (mirror) {
+        Pc.mir = reinterpret_cast<cplx<T>*>(ctx->d_mirror);
+        for (int sd = 0; sd < 2; ++sd) {
+          Pc.side0 = sd;
+          Pc.mirror = 1 + sd;
+          k_pair_chain_pr<T, N, LP><<<dim3(nj_items * P.sc, 1), PrCfg<T, N>::threads,
+                                      PrSmem<T, N, LP, 2, 3>::bytes, st>>>(Pc);
+        }
+        nl[3] += 1;
+      } else if (pruned) {
         k_pair_chain_pr<T, N, LP><<<dim3(nj_items * P.sc, nsides), PrCfg<T, N>::threads,
                                     PrSmem<T, N, LP, 2, 3>::bytes, st>>>(Pc);
+      }
     }
     if constexpr (CLc > 0) {
       if (dist_chain)

@@ -31,6 +31,9 @@ template <int N, int L> struct Sup {
   static __host__ __device__ constexpr int mil(int c) {
     return (L == N) ? (c <= (N - 1) / 2 ? c : c - N) : (c < H ? c : c - L);
   }
+  // compact index of the negated Miller integer (L < N: the support is symmetric and clear of the
+  // Nyquist index, so -m is again on the support)
+  static __host__ __device__ constexpr int refl(int c) { return c == 0 ? 0 : L - c; }
   static __device__ __forceinline__ int bidx(int c1, int i2, int i3) { return (c1 * N + i2) * P + i3; }
   static __device__ __forceinline__ int cidx(int c1, int c2, int c3) { return (c1 * L + c2) * L + c3; }
 };
@@ -176,6 +179,21 @@ template <int N, int L> __device__ __forceinline__ int gidx_c(int c1, int c2, in
 //   for d: b = FT^{-1}[U^ap_d A];  C += -U^ap_d FT[tw3b6 n b]             (3b6, antiparallel)
 //   acc += f ket_q FT^{-1}[C - tw2ax V A]                                 (3b3, 2bx2, 3b5, 3b6, 2ax)
 // (Algs. 2, 5, 6, 9, 11, 12 and the 2bx terms of Sec. 2.6.3.)
+//
+// Mirrored two-sided launches (P.mirror; Eq. BITCSCFconj).  The left pair density of (output q,
+// partner j) is conj(phi_j^* chi_q) -- the complex conjugate of the right pair density of (output j,
+// partner q) -- and the left side's kernel momentum is -(k_j - k_q + G), so on a support symmetric
+// under G -> -G its compact spectrum is A_L(c) = conj(A_R(refl c)).  With u~ real and even,
+// U_d(-p) = conj(U_d(p)), so FT^{-1}[U^ap_d A_L] = conj(FT^{-1}[U^ap_d A_R]); the left density is
+// conj of the right one, so the antiparallel 3b6 spectrum is C_ap,L(c) = conj(C_ap,R(refl c)) too.
+// mirror = 1 (right launch): a CTA whose output j is itself a partner (band < no) stores both
+// reflections for the left pair (q, j), the antiparallel one summed over d as it is emitted;
+// mirror = 2 (left launch, after it): such a pair loads them as its A and initial C and skips its
+// own pair-density transform and antiparallel loop (7 of its 14 transforms).  Left outputs whose
+// right counterpart was skipped for a zero occupation compute their own.  The parallel-spin loop
+// and the final transform stay per side: their partner fields (Y, Z, h3b, V) have no such
+// relation.  Built for FP64, whose chains are bound by the FP64 pipe; in FP32 the parallel-spin
+// passes' loads dominate and the mirror code is compiled out.
 template <typename T, int N, int L>
 __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Params<T> P) {
   using G = Geo<N>;
@@ -184,10 +202,18 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
   constexpr int CH = 1;   // elements per load chunk of the pointwise pass (1 measured fastest in FP32)
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T red[32];
-  const SideArgs<T>& SD = P.side[blockIdx.y];
+  const SideArgs<T>& SD = P.side[P.side0 + blockIdx.y];
   const int jitem = blockIdx.x / P.sc, chunk = blockIdx.x % P.sc;
   const int jo = P.sym ? P.irr[jitem / P.nb] * P.nb + jitem % P.nb : jitem, j = P.j0 + jo, kj = j / P.nb;
   const int M = P.Nk * P.no, nj = P.nj_out;
+  // mirrored launches (FP64 only: the FP32 kernel is bound by the loads of its parallel-spin
+  // passes, which both sides keep, and gains nothing from them): output j as a partner index; write
+  // (right) or read (left) the reflections
+  constexpr bool MIR = sizeof(T) == 8;
+  const int jocc = kj * P.no + j % P.nb;
+  const bool mw = MIR && P.mirror == 1 && j % P.nb < P.no;
+  // (the right CTA of output q skipped its pair with j when f_j, in the compute precision, was 0)
+  const bool mr = MIR && P.mirror == 2 && j % P.nb < P.no && (T)(P.occ[j] / P.Nk) != T(0);
   const int qi_begin = (int)((long long)chunk * M / P.sc), qi_end = (int)((long long)(chunk + 1) * M / P.sc);
   cplx<T>* B = reinterpret_cast<cplx<T>*>(smraw);
   cplx<T>* A;
@@ -251,11 +277,25 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
     const cplx<T>* ketq = SD.ket + (size_t)q * NN;
     const cplx<T>* Zq = SD.Z + ((size_t)(kq * P.no + mu) * 3) * NN;
     const cplx<T>* h3bq = SD.h3b + ((size_t)(kq * P.no + mu) * 3) * NN;
-    // A = FT[conj(bra_q) ket_j] on the support
-    pass_axis1<T, N, L, false>(
-        B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ketj + g), ldg(braq + g)); },
-        [&](int, int, cplx<T>(&)[N]) {}, true);
-    pfwd_32<T, N, L>(B, [&](int c1, int c2, int c3, cplx<T> v) { A[S::cidx(c1, c2, c3)] = P.invN * v; });
+    // the reflections of this pair: [A][C_ap] of the left pair (q, j) (write) or of this one (read)
+    cplx<T>* MA = (mw || mr) ? P.mir + ((size_t)(mw ? qi : jocc) * M + (mw ? jocc : qi)) * 2 * S::cvol : nullptr;
+    if (mr) {
+      for (int c = threadIdx.x; c < S::cvol; c += blockDim.x) {
+        A[c] = MA[c];
+        C[c] = need_ap ? MA[S::cvol + c] : cplx<T>{0, 0};
+      }
+      __syncthreads();
+    } else {
+      // A = FT[conj(bra_q) ket_j] on the support
+      pass_axis1<T, N, L, false>(
+          B, [&](int a, int b, int c) { const int g = G::gidx(a, b, c); return mulc(ldg(ketj + g), ldg(braq + g)); },
+          [&](int, int, cplx<T>(&)[N]) {}, true);
+      pfwd_32<T, N, L>(B, [&](int c1, int c2, int c3, cplx<T> v) {
+        const cplx<T> a = P.invN * v;
+        A[S::cidx(c1, c2, c3)] = a;
+        if (mw) MA[S::cidx(S::refl(c1), S::refl(c2), S::refl(c3))] = conjg(a);
+      });
+    }
     if (P.div && kq == kj && t3b6 != T(0)) {
       // O_qj = A(0) and X_s = sum_{G != 0} u~_s(G) A(G) n~(-G) for the 3b6 corrections
       for (int s = 0; s < 2; ++s) {
@@ -279,11 +319,13 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
       }
       __syncthreads();
     }
+    // spin channels: parallel then antiparallel (a reading mirrored CTA has the antiparallel
+    // spectrum in C already; a writing one also sums it, reflected, into the left pair's slot)
     for (int sp = 0; sp < 2; ++sp) {
       if (sp == 0 && !(need_pp || need_F)) continue;
-      if (sp == 1 && !need_ap) continue;
+      if (sp == 1 && (!need_ap || mr)) continue;
       for (int d = 0; d < 3; ++d) {
-        const bool first_C = (sp == 0 && d == 0);
+        const bool first_C = sp == 0 && d == 0 && !mr;
         const PComp<T> qd = pcomp_setup<T>(P, dl, d);
         // b = FT^{-1}[U_d A]
         pinv_23<T, N, L>(B, [&](int c1, int c2, int c3) {
@@ -340,6 +382,11 @@ __global__ void __launch_bounds__(PrCfg<T, N>::threads, 1) k_pair_chain_pr(Param
           const cplx<T> t = mul_si<T, -1>(k * v);
           const int s = S::cidx(c1, c2, c3);
           C[s] = first_C ? t : C[s] + t;
+          if (sp == 1 && mw) {
+            // the thread that emits an index emits it for every d
+            cplx<T>* mc = MA + S::cvol + S::cidx(S::refl(c1), S::refl(c2), S::refl(c3));
+            *mc = d == 0 ? conjg(t) : *mc + conjg(t);
+          }
         });
       }
     }

@@ -231,6 +231,14 @@ class Context:
         _lib.check(self.lib, self.h, self.lib.tc_pair_kernels(self.h, info))
         return {s: tuple(info[3 * i: 3 * i + 3]) for i, s in enumerate(("pair_chain", "pair_3b4", "occ_pairs"))}
 
+    def pair_mirror(self):
+        """(active, bytes): whether two-sided applies take the left pair spectra from the right ones
+        (tc_pair_mirror)."""
+        a = ctypes.c_int()
+        b = ctypes.c_ulonglong()
+        _lib.check(self.lib, self.h, self.lib.tc_pair_mirror(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return bool(a.value), int(b.value)
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.tc_destroy(self.h)

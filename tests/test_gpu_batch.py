@@ -2,7 +2,8 @@
 
 Cells from the HEG batch recipe (synth.heg_batch: uneven boxes 16^3-32^3,
 1-8 k-points, 7-33 plane waves per k), FP32:
-* every cell's output equals a single-cell tc_apply of the same inputs bit for bit;
+* every cell's output equals a single-cell tc_apply of the same inputs bit for bit (single-cell
+  contexts without the mirrored pair chains, TC_FAULT=nomirror, as batch cells run them);
 * plane-wave orbitals: every output is diagonal in momentum and out_L = out_R (BITC = TC);
 * the two cheapest cells against the FP64 oracle (1e-5), and for every box size of the recipe the
   cheapest cell of the 256, batched together, against the oracle (1e-5);
@@ -51,9 +52,10 @@ def batch():
     bc.close()
 
 
-def test_batch_equals_single_cell_calls(batch):
+def test_batch_equals_single_cell_calls(batch, monkeypatch):
     from paper_2302_07420_gb300.operator import Context
     cells, data, bc, d, res = batch
+    monkeypatch.setenv("TC_FAULT", "nomirror")   # batch cells hold no reflection buffer
     for i, (p, (S, c, occ)) in enumerate(zip(cells, data)):
         ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
                       precision="fp32")
