@@ -681,6 +681,7 @@ def main():
     torch.cuda.synchronize()
     ms64 = e0.elapsed_time(e1) / args.fp64_steps
     pc64_ms, pc64_launch = ctx64.stage_times()["pair_chain"]
+    mirrored64 = ctx64.pair_mirror()[0]
     ctx64.profile(False)
     achieved64 = flop_per_apply / (pc64_ms / 1e3 / args.fp64_steps) / 1e12
     ref_scale = max(float(r64.abs().max()), float(l64.abs().max()))
@@ -757,7 +758,11 @@ def main():
             "clocks": clk.summary(),
             "fp64": {"value": npairs / (ms64 / 1e3), "unit": "pairs/s", "ms_per_step": ms64,
                      "steps": args.fp64_steps, "pair_chain_tflops": achieved64,
-                     "pair_chain_frac_of_measured_fp64_peak": achieved64 / peak64},
+                     "pair_chain_frac_of_measured_fp64_peak": achieved64 / peak64,
+                     "pair_chain_ms_per_apply": pc64_ms / args.fp64_steps,
+                     "pair_chain_launches_per_apply": pc64_launch / args.fp64_steps,
+                     "mirrored": mirrored64,
+                     "flop_convention": "algorithmic (14 transforms per pair chain); mirrored left chains run 7"},
             "error": {"fp32_vs_fp64_gpu_max_rel": err32, "fp64_gpu_vs_oracle_sampled_max_rel": err_oracle,
                       "energy_fp32_vs_fp64_ha_per_electron": err_e, "energy_fp64_ha_per_cell": e64,
                       "bf16_store_vs_fp64_gpu_max_rel": err_bf16,
