@@ -629,17 +629,15 @@ int injected_fault(const char* site) {
 // saves.)
 static void alloc_mirror(tc_ctx* c) {
   const Setup& S = c->S;
-  if (c->prec != TC_FP64) return;
-  if (S.nkb > 0 || c->plan_prune_L <= 0 || c->pair_support > c->plan_prune_L) return;
   if (injected_fault("mirror") != TC_OK) return;
-  const size_t L = (size_t)c->plan_prune_L, M = (size_t)S.Nk * S.no;
-  const size_t bytes = M * M * 2 * L * L * L * c->esz;
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
-  if (bytes > fr / 4) return;
+  const size_t bytes =
+      mirror_buffer_bytes(c->prec == TC_FP64, S.nkb, c->plan_prune_L, c->pair_support, S.Nk, S.no, fr);
+  if (bytes == 0) return;
   if (cudaMalloc(&c->d_mirror, bytes) != cudaSuccess) {
     cudaGetLastError();
     c->d_mirror = nullptr;

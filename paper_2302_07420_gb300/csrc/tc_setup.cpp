@@ -288,6 +288,13 @@ bool left_from_right_exact(int n, int span) { return n % 2 == 1 || span <= n / 2
 
 int pair_support_len(int n, int span) { return std::min(n, 2 * span + 1); }
 
+size_t mirror_buffer_bytes(bool fp64, int nkb, int prune_L, int pair_support, int Nk, int no, size_t free_bytes) {
+  if (!fp64 || nkb > 0 || prune_L <= 0 || pair_support > prune_L || Nk <= 0 || no <= 0) return 0;
+  const size_t L = (size_t)prune_L, M = (size_t)Nk * no;
+  const size_t bytes = M * M * 2 * L * L * L * 16;
+  return bytes <= free_bytes / 4 ? bytes : 0;
+}
+
 int smallest_near_best(const double* t, int n) {
   double best = 1e300;
   for (int s = 1; s <= n; ++s) best = std::min(best, t[s]);

@@ -89,6 +89,11 @@ bool left_from_right_exact(int n, int span);
 // Box indices per axis that a pair-density spectrum can occupy: min(n, 2 span + 1).  The pruned
 // transforms of the pair chains apply when this is at most their compiled support length.
 int pair_support_len(int n, int span);
+// Bytes of the reflection buffer of mirrored two-sided pair chains (k_pair_chain_pr, mirror), or 0
+// for none: FP64 contexts on the SCF mesh (no band points) whose pair chains take the pruned
+// transforms (0 < prune_L, pair_support <= prune_L), (Nk no)^2 x 2 x prune_L^3 complex FP64 values,
+// allocated only when that is at most a quarter of free_bytes.
+size_t mirror_buffer_bytes(bool fp64, int nkb, int prune_L, int pair_support, int Nk, int no, size_t free_bytes);
 
 // Appendix B kernel pieces (host, FP64), exposed for the table tests.
 double host_u_tilde(double p2, double A, double C);

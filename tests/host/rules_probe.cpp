@@ -3,6 +3,7 @@
 //   near <n> <t1> ... <tn>                  -> prints smallest_near_best
 //   span <count> <m1 m2 m3> x count         -> prints miller_span of one sphere of count vectors
 //   grid <n> <span>                          -> prints left_from_right_exact and pair_support_len
+//   mirror <fp64> <nkb> <L> <support> <Nk> <no> <free> -> prints mirror_buffer_bytes
 // from standard input and prints one integer per line.
 #include <cstdio>
 #include <array>
@@ -39,6 +40,11 @@ int main() {
       int n = 0, span = 0;
       if (std::scanf("%d %d", &n, &span) != 2) return 2;
       std::printf("%d %d\n", tc::left_from_right_exact(n, span) ? 1 : 0, tc::pair_support_len(n, span));
+    } else if (!std::strcmp(cmd, "mirror")) {
+      int fp64 = 0, nkb = 0, L = 0, sup = 0, nk = 0, no = 0;
+      unsigned long long fr = 0;
+      if (std::scanf("%d %d %d %d %d %d %llu", &fp64, &nkb, &L, &sup, &nk, &no, &fr) != 7) return 2;
+      std::printf("%llu\n", (unsigned long long)tc::mirror_buffer_bytes(fp64 != 0, nkb, L, sup, nk, no, (size_t)fr));
     } else {
       return 2;
     }

@@ -3,8 +3,9 @@ count (pick_split: best filled last wave of CTAs on the SMs), the autotuner's ch
 counts (smallest_near_best: the smallest count within 2 % of the fastest), and the grid rules that
 tc_init and tc_apply_noalloc share: the Miller span of the spheres, whether the left occupied-pair
 fields are exact conjugates of the right ones (odd box or span <= n/2 - 1), and the pair-density
-support length min(n, 2 span + 1) that selects the pruned pair-chain transforms.  A probe compiled
-from the library's source answers queries; the expected values restate the rules.
+support length min(n, 2 span + 1) that selects the pruned pair-chain transforms, and the size of the
+reflection buffer of mirrored FP64 pair chains (or none).  A probe compiled from the library's source
+answers queries; the expected values restate the rules.
 """
 import math
 import os
@@ -99,3 +100,22 @@ def test_grid_rules(probe):
     # the si_k444 grid: span 8 on 24^3 is clear of the Nyquist planes and fills the 17-index support
     assert pairs[cases.index((24, 8))] == (1, 17)
     assert pairs[cases.index((24, 9))] == (1, 19) and pairs[cases.index((24, 12))] == (0, 24)
+
+
+def test_mirror_buffer_rule(probe):
+    """FP64 mesh contexts on the pruned transforms: (Nk no)^2 x 2 x L^3 x 16 bytes when at most a quarter
+    of the free memory; nothing in FP32, with band points, without pruned transforms or when it does not fit."""
+    gib = 1 << 30
+    cases = [(1, 0, 17, 17, 64, 4, 280 * gib), (0, 0, 17, 17, 64, 4, 280 * gib), (1, 1, 17, 17, 64, 4, 280 * gib),
+             (1, 0, 0, 21, 64, 4, 280 * gib), (1, 0, 17, 19, 64, 4, 280 * gib), (1, 0, 17, 17, 64, 4, 30 * gib),
+             (1, 0, 13, 13, 2, 2, 1 * gib), (1, 0, 17, 9, 2, 3, 4 * gib)]
+    got = probe(["mirror %d %d %d %d %d %d %d" % c for c in cases])
+
+    def rule(fp64, nkb, L, sup, nk, no, free):
+        if not fp64 or nkb > 0 or L <= 0 or sup > L:
+            return 0
+        b = (nk * no) ** 2 * 2 * L ** 3 * 16
+        return b if b <= free // 4 else 0
+    assert got == [rule(*c) for c in cases]
+    assert got[0] == 256 ** 2 * 2 * 17 ** 3 * 16    # si_k444 FP64: 10.3 GB
+    assert got[5] == 0                              # 30 GiB free: does not fit in a quarter
