@@ -531,6 +531,10 @@ def main():
                          "256-cell batch (one graph launch per step) and prints its own line")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint and 48^3 timings added to the line")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="with --profile-run: the context's precision (the timed line is always FP32 + FP64)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="with --profile-run: default partner chunks instead of tc_autotune's")
     ap.add_argument("--profile-run", action="store_true",
                     help="FP32 applies only (warm-up + steps), no JSON line: the ncu capture command")
     ap.add_argument("--symmetric", action="store_true",
@@ -564,7 +568,7 @@ def main():
     p = (synth.WORKLOADS["si_k444"]() if args.workload == "si_k444"
          else synth.si_params(kmesh=(4, 4, 2) if args.workload == "si_k442" else (2, 2, 2)))
     ctx = Context(p["lattice"], p["kmesh"], p["ecut"], p["fft"], p["nbands"], p["nocc"], p["A"], p["C"],
-                  precision="fp32")
+                  precision=args.precision if args.profile_run else "fp32")
     npw, miller = ctx.layout()
     c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 1, kpg_list(p["lattice"], p["kmesh"], miller, npw),
                                          ctx.npw_max, p["nbands"])
@@ -583,7 +587,7 @@ def main():
             dist.barrier()
 
     # partner-chunk counts of the two-sided apply measured on this workload (setup, outside the timed region)
-    so_sc = ctx.autotune(d_phi, d_chi, occ)
+    so_sc = None if (args.profile_run and args.no_autotune) else ctx.autotune(d_phi, d_chi, occ)
     if args.profile_davidson:
         for _ in range(args.warmup + args.steps):
             ctx.davidson_step(d_phi, d_chi, occ)
