@@ -58,7 +58,9 @@ with them and fails if one sign of a pair is wrong.
 Pins: tests/test_oracle_band.py (4 pi Gamma_b/Omega against an independent
 phased Ewald sum, alpha-independence of Gamma_b and W, a band point on the
 mesh reproduces the SCF operator, HEG closed forms off the mesh, direct sums,
-adjointness at the band point, planted sign errors in each adjoint pair).
+adjointness at the band point, planted sign errors in each adjoint pair, and
+next to a mesh point every term has a finite limit with the corrections while
+the uncorrected terms diverge).
 """
 import math
 

@@ -27,7 +27,8 @@ for alpha; the reading used here is sqrt(alpha) = L_min / 12 with L_min the
 shortest lattice vector of the Born-von Karman supercell, and the primed sum
 runs over every reciprocal vector of that supercell until exp(-alpha p^2) < 1e-20.
 
-Parity pins: sphere sizes and ordering are compared bit-exactly with the CUDA
+Parity pins: sphere counts on the cutoff (inclusive; lattice-point counts of
+the simple-cubic cell), sizes and ordering compared bit-exactly with the CUDA
 library's layout; Gamma0 is pinned by an independent Ewald sum (4 pi Gamma0 /
 Omega = -v_Madelung of the supercell) and by the simple-cubic Madelung constant.
 """

@@ -43,7 +43,8 @@ return their own eigenvalues; Appendix A (the Gram-Schmidt of eigenvectors
 keeps the eigenvalues on the diagonal and zeros below it); z^H y = I and
 the eigen-equations; plane waves of the homogeneous electron gas are exact
 eigenvectors of the TC operator, with the closed-form eigenvalues; the
-Payne factor's values and limits.
+Payne factor's values and limits, its argument for one- and two-wave trial
+vectors, and the 1e-8 norm cut on both sides.
 """
 import copy
 

@@ -35,7 +35,8 @@ holds for any t without truncation error.  dK comes from
 transforms of Sec. 2.6.3 and Appendix B).
 
 Parity pins (tests/test_oracle_gradient.py): the orbital gradient against an
-exact 4-point stencil of E along random directions, corrections on and off;
+exact 4-point stencil of E along random directions, corrections on and off,
+and with occupations that differ between k-points;
 dE/dA_s against the exact 3-point difference of E (E is quadratic in A_s at
 fixed C); dE/dC_s against Richardson-extrapolated central differences of E;
 the degree-2 claim along dK; each kernel derivative against central

@@ -9,6 +9,8 @@
   occupied plane waves of the mesh, derived by hand from the algorithms (Sec. 2.6), plus the band
   corrections (Eqs. divcorr_2ax_band, 3b6_div_band1, divcorr_2bx1/2, div_corr_3a4_2/3, 3b5_div_2/3,
   div_corr_3b4_2/4);
+* next to a mesh point (k_b = k_m + delta, delta -> 0) every term has a finite limit with the band
+  corrections and diverges without them;
 * the FFT route equals direct reciprocal-space sums at a band point; adjointness at the band point, which
   also fails when one member of a pair of grad-u band corrections (2bx1/2bx2, 3a3/3b3, 3a4/3b5,
   3b6 band2/band3) or a 3b4 correction has the wrong sign.
@@ -136,6 +138,53 @@ def test_adjointness_at_a_band_point(div):
 # 3b4 becomes a_b.a_b - 2 i c o_n (W.a_b) - c^2 o_n^2 (W.W); those of 3a3, 3b3 and 3b6 (band2/3) vanish
 # (h1 = 0, and n~ has only its G = 0 component).
 # ---------------------------------------------------------------------------------------------------
+
+def _near_mesh(div, deltas, general=False, m=1):
+    """Band operator at k_b = k_m + delta e next to the mesh point k_m, with k_m's own orbitals as the band
+    point's (its sphere is the same for these delta), A_pp != A_ap.  general: left orbitals that are not
+    biorthonormal to the right ones (the general-overlap forms) and occupations that differ between
+    k-points."""
+    p = synth.tiny_params(2, kmesh=(1, 1, 2), fft=(8, 9, 10), ecut=1.2, nbands=3, nocc=2, scale=5.0)
+    S = make_setup(p, A=[p["A"][0], 1.6 * p["A"][0]], div_correction=div)
+    c_phi, c_chi = synth.random_orbitals(synth.SEED0 + 62, [S.kpG(k) for k in range(S.Nk)], S.npw_max,
+                                         S.nbands, perturb=0.2)
+    occ = synth.occupations(S.Nk, S.nbands, S.nocc)
+    occ[:, 1] = 0.6
+    if general:
+        rng = np.random.default_rng(synth.SEED0 + 63)
+        for k in range(S.Nk):
+            n = S.npw[k]
+            c_chi[k, :, :n] += 0.15 * (rng.standard_normal((S.nbands, n)) + 1j * rng.standard_normal((S.nbands, n)))
+        occ[m, 1] = 0.85
+    e = np.array([0.31, -0.52, 0.79])
+    e /= np.linalg.norm(e)
+    out = []
+    for d in deltas:
+        kb = S.kfrac[m] + d * e
+        SB = BD.BandSetup(S, kb)
+        assert np.array_equal(SB.miller[S.Nk], S.miller[m])
+        out.append(BD.band_apply(S, c_phi, c_chi, occ, kb, c_phi[m:m + 1], c_chi[m:m + 1], occ[m:m + 1]))
+    return out
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_band_corrections_cancel_the_singularity_next_to_a_mesh_point(general):
+    """Off the mesh every q + G is kept in the sums, and the partner q = k_m enters with the kernel at
+    p = k_b - k_m, which diverges as k_b -> k_m: 4 pi/p^2 in 2ax and, through U U, in 3b6; i p u~(p) ~ 1/p
+    in the grad-u terms.  The band corrections (Gamma_b of Eq. divcorr_2ax_band and 3b6_div_band1, the
+    vector sum W of Eq. correction_nabla in the grad-u and 3b6 band2/3 forms) carry the same singular
+    parts with the opposite sign, so with them every term has a finite limit; without them the terms
+    grow as 1/delta or 1/delta^2.  A wrong sign or amplitude of any correction (W, Gamma_b, A_pp against
+    A_ap) leaves a divergent remainder."""
+    near = _near_mesh(1, (1e-3, 1e-4), general)
+    bare = _near_mesh(0, (1e-3, 1e-4), general)
+    scale = max(np.abs(near[0][t]).max() for t in OP.TERMS)
+    for t in OP.TERMS:
+        a, b = near[0][t], near[1][t]
+        assert np.abs(b - a).max() <= 0.02 * max(np.abs(a).max(), 1e-3 * scale), t
+    for t in ("2ax", "2bx1", "2bx2", "3a3", "3a4", "3b3", "3b4", "3b5", "3b6"):
+        assert np.abs(bare[1][t]).max() > 5.0 * np.abs(bare[0][t]).max(), t      # the singular terms are there
+
 
 def _heg_band_case(kmesh=(2, 2, 1), nbands=9, A=None):
     p = synth.heg_params(14, 4.0, 12, 4)

@@ -54,6 +54,18 @@ def test_sphere_counts_and_order():
     assert S.npw.sum() == sum(len(CL.sphere_miller(S.kcart[k] + S.B[0], S.B, S.ecut)) for k in range(S.Nk))
 
 
+def test_sphere_cutoff_is_inclusive():
+    """A plane wave exactly on the cutoff belongs to the sphere (|k+G|^2/2 <= E_cut).  On the simple-cubic
+    cell of edge 2 pi (b_i = unit vectors, so |G|^2 = |m|^2 exactly in floating point) at Gamma, the sphere
+    of E_cut = r2/2 holds the integer vectors with |m|^2 <= r2: the cumulative sums of r3(n), the number of
+    representations of n as a sum of three squares (1, 6, 12, 8, 6, 24, 24, 0, 12, 30 for n = 0..9)."""
+    counts = {1: 7, 2: 19, 3: 27, 4: 33, 5: 57, 6: 81, 7: 81, 8: 93, 9: 123}
+    B = CL.reciprocal(2.0 * np.pi * np.eye(3))
+    assert np.array_equal(B, np.eye(3))
+    for r2, want in counts.items():
+        assert len(CL.sphere_miller(np.zeros(3), B, 0.5 * r2)) == want, r2
+
+
 def test_kmesh_and_box_conventions():
     f = CL.kmesh_frac((4, 1, 3))
     assert f.shape == (12, 3)

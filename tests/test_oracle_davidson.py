@@ -39,6 +39,50 @@ def test_payne_values_and_limits():
     np.testing.assert_allclose(DV.payne(big) * 2 * big, 1.0, rtol=2e-3)   # -> 1/(2x)
 
 
+def test_payne_argument_is_the_kinetic_energy_ratio_of_the_trial_vector():
+    """Sec. 2.4: x(G) = |k+G|^2/2 divided by the trial vector's own kinetic energy sum |k+G'|^2/2 |v(G')|^2.
+
+    For a trial vector that is one plane wave G0 that energy is t(G0), so the new direction is
+    P(t(G)/t(G0)) (h v - eps v), with eps = h(G0, G0) and no component along G0 (the residual has none
+    and P(1) keeps it zero); for a two-wave vector (a e_0 + b e_2)/norm it is (0.3 |a|^2 + 0.7 |b|^2)/norm^2."""
+    rng = np.random.default_rng(41)
+    t = np.array([0.3, 0.0, 0.7, 1.9, 4.2, 2.5])
+    H = _rand_c(rng, 6, 6)
+    v = np.zeros((1, 6), complex)
+    v[0, 0] = 1.0
+    kept, idx = DV.new_directions(v, v @ H.T, t)
+    assert idx == [0]
+    r = H[:, 0] - H[0, 0] * v[0]
+    want = DV.payne(t / 0.3) * r
+    want /= np.linalg.norm(want)
+    np.testing.assert_allclose(_phase_align(want[None], kept[0][None])[0], want, atol=1e-13)
+    # two plane waves: kinetic energy (0.3 * 1 + 0.7 * 4) / 5 = 0.62
+    v = np.zeros((1, 6), complex)
+    v[0, 0], v[0, 2] = 1.0 / np.sqrt(5.0), 2.0 / np.sqrt(5.0)
+    kept, _ = DV.new_directions(v, v @ H.T, t)
+    hv = v[0] @ H.T
+    u = DV.payne(t / 0.62) * (hv - np.vdot(v[0], hv) * v[0])
+    u -= np.vdot(v[0], u) * v[0]
+    u /= np.linalg.norm(u)
+    np.testing.assert_allclose(_phase_align(u[None], kept[0][None])[0], u, atol=1e-13)
+
+
+@pytest.mark.parametrize("eps,kept", [(1e-6, True), (1e-11, False)])
+def test_norm_cut_of_new_directions(eps, kept):
+    """Sec. 2.4: a new direction whose norm after orthogonalisation is below 1e-8 is left out, one above
+    it is kept.  h = diag(t) + eps X with v = e_0 leaves a residual of norm ~eps (P is 0.6-0.8 here)."""
+    rng = np.random.default_rng(43)
+    t = np.array([0.5, 0.55, 0.6, 0.7, 0.8])
+    X = _rand_c(rng, 5, 5)
+    H = np.diag(t).astype(complex) + eps * X
+    v = np.zeros((1, 5), complex)
+    v[0, 0] = 1.0
+    new, _ = DV.new_directions(v, v @ H.T, t)
+    nrm = np.linalg.norm(DV.payne(t / 0.5) * (H[:, 0] - H[0, 0] * v[0]))
+    assert (1e-7 < nrm < 1e-4) if kept else (nrm < 1e-9)
+    assert len(new) == (1 if kept else 0)
+
+
 # ---------------------------------------------------------------- eigen-decomposition
 def test_eig_sorted_equations_and_order():
     rng = np.random.default_rng(1)

@@ -113,10 +113,15 @@ def test_dE_dC_matches_extrapolated_differences_of_E(ushort_factor):
         assert abs(g["C"][s] - ref) < 1e-8 * abs(ref), (s, g["C"][s], ref)
 
 
-@pytest.mark.parametrize("div,ushort_factor", [(1, 1.0), (1, 2.0), (0, 1.0)])
-def test_orbital_gradient_is_exact(div, ushort_factor):
-    """g_phi, g_chi against the exact 4-point stencil of E along random directions (E is cubic)."""
+@pytest.mark.parametrize("div,ushort_factor,kdep", [(1, 1.0, False), (1, 2.0, False), (0, 1.0, False),
+                                                    (1, 1.0, True)])
+def test_orbital_gradient_is_exact(div, ushort_factor, kdep):
+    """g_phi, g_chi against the exact 4-point stencil of E along random directions (E is cubic).
+    kdep: occupations that differ between the two k-points, so that a weight taken at the wrong k-point
+    (f of the output k instead of the partner's, of q1 instead of q2) breaks the identity."""
     p, S, c_phi, c_chi, occ = tiny(seed=4, div=div, ushort_factor=ushort_factor, fill=(1.0, 0.55))
+    if kdep:
+        occ[1, :2] = (0.8, 0.35)
     g_phi, g_chi = GR.orbital_gradient(S, c_phi, c_chi, occ)
     rng = np.random.default_rng(5)
     mask = np.zeros((S.Nk, 1, S.npw_max))
