@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 from conftest import make_setup
+from oracle import band as BD
 from oracle import kernels as KN
 from oracle import operator as OP
 from paper_2302_07420_gb300 import synth
@@ -53,9 +54,24 @@ def _run(probe, tmp_path, p, div=1, uf=1.0, alpha=0.0):
     hartV = x[o:o + 2 * N].reshape(2, N); o += 2 * N
     hartU = x[o:o + N]; o += N
     hartUs = x[o:o + 2 * N].reshape(2, N); o += 2 * N
+    npw_max = int(x[o]); o += 1
+    npw = x[o:o + Nk].astype(int); o += Nk
+    miller = x[o:o + Nk * npw_max * 3].astype(int).reshape(Nk, npw_max, 3); o += Nk * npw_max * 3
+    box = x[o:o + Nk * npw_max].astype(int).reshape(Nk, npw_max); o += Nk * npw_max
+    deriv = []
+    for _ in range(4):
+        d = {}
+        for key, size, shape in (("tabV", nd * 2 * N, (nd, 2, N)), ("tabU", nd * 2 * N, (nd, 2, N)),
+                                 ("hartV", 2 * N, (2, N)), ("hartU", N, (N,)), ("hartUs", 2 * N, (2, N))):
+            d[key] = x[o:o + size].reshape(shape); o += size
+        d["corr"], d["amp"] = x[o:o + 2], x[o + 2:o + 4]; o += 4
+        deriv.append(d)
+    gsq0 = x[o]; o += 1
+    band = dict(found=bool(x[o]), gamma_b=x[o + 1], W=x[o + 2:o + 5]); o += 5
     assert o == len(x)
     return dict(Omega=Om, alpha=al, Gamma0=G0, corr=(c0, c1), Nk=Nk, did=did, delta=delta, tabV=tabV, tabU=tabU,
-                hartV=hartV, hartU=hartU, hartUs=hartUs)
+                hartV=hartV, hartU=hartU, hartUs=hartUs, npw_max=npw_max, npw=npw, miller=miller, box=box,
+                deriv=deriv, gsq0=gsq0, band=band)
 
 
 CASES = {
@@ -79,16 +95,21 @@ def test_host_tables_match_the_oracle(probe, tmp_path, name, div, uf):
     for s in range(2):
         ref = ks.corr(s, S.Gamma0, S.ushort_factor, S.Nk)
         assert abs(T["corr"][s] - ref) < 1e-12 * max(abs(ref), 1e-30), (s, T["corr"][s], ref)
+    _compare_tables(T, S, KN.JastrowKernels(S.A, S.C))
+
+
+def _compare_tables(T, S, ks):
+    """Exchange and Hartree-type tables of the probe (T) against the oracle's kernels with kernel data ks."""
     c_phi = np.zeros((S.Nk, S.nbands, S.npw_max), complex)
-    right = OP.TCOperator(S, c_phi, c_phi, np.zeros((S.Nk, S.nbands)), left=False)
-    left = OP.TCOperator(S, c_phi, c_phi, np.zeros((S.Nk, S.nbands)), left=True)
+    right = OP.TCOperator(S, c_phi, c_phi, np.zeros((S.Nk, S.nbands)), left=False, kset=ks)
+    left = OP.TCOperator(S, c_phi, c_phi, np.zeros((S.Nk, S.nbands)), left=True, kset=ks)
     P = S.Gbox.reshape(-1, 3)
     for ko in range(S.Nk):
         for kp in range(S.Nk):
             i = T["did"][ko, kp]
             np.testing.assert_allclose(T["delta"][i], S.kcart[ko] - S.kcart[kp], rtol=0, atol=1e-14)
             KR, KL = right.kern(ko, kp), left.kern(ko, kp)
-            sc = np.abs(KR["V"]).max()
+            sc = max(np.abs(KR["V"]).max(), 1e-300)
             np.testing.assert_allclose(T["tabV"][i, 0], KR["V"].ravel(), rtol=0, atol=1e-13 * sc)
             np.testing.assert_allclose(T["tabV"][i, 1], KL["V"].ravel(), rtol=0, atol=1e-13 * sc)
             p = T["delta"][i][None, :] + P
@@ -98,10 +119,75 @@ def test_host_tables_match_the_oracle(probe, tmp_path, name, div, uf):
                 np.testing.assert_allclose(lib, U, rtol=0, atol=1e-13 * max(np.abs(U).max(), 1e-30))
     VhR, UhR, usR = right.hartree_kernels()
     VhL, _, _ = left.hartree_kernels()
-    sc = np.abs(VhR).max()
+    sc = max(np.abs(VhR).max(), 1e-300)
     np.testing.assert_allclose(T["hartV"][0], VhR.ravel(), rtol=0, atol=1e-13 * sc)
     np.testing.assert_allclose(T["hartV"][1], VhL.ravel(), rtol=0, atol=1e-13 * sc)
     for s in range(2):
-        np.testing.assert_allclose(T["hartUs"][s], usR[s].ravel(), rtol=0, atol=1e-13 * np.abs(usR[s]).max())
+        np.testing.assert_allclose(T["hartUs"][s], usR[s].ravel(), rtol=0,
+                                   atol=1e-13 * max(np.abs(usR[s]).max(), 1e-300))
     np.testing.assert_allclose(T["hartU"], (usR[0] + usR[1]).ravel() / S.Omega, rtol=0,
-                               atol=1e-13 * np.abs(T["hartU"]).max())
+                               atol=1e-13 * max(np.abs(T["hartU"]).max(), 1e-300))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_derivative_tables_match_the_oracle(probe, tmp_path, name):
+    """The tables of dK/dA_s and dK/dC_s (kernel_data modes KD_DA_PP .. KD_DC_AP, which the adjoint uses)
+    against the oracle's closed-form derivatives (oracle/kernels.py, pinned against differences of the
+    kernels), including the correction coefficients and amplitudes; the Coulomb part and the other
+    channel carry no derivative."""
+    p = CASES[name]()
+    if name.startswith("heg"):      # unequal channels, so that a channel mix-up shows
+        p["A"], p["C"] = [p["A"][0], 1.3 * p["A"][1]], [p["C"][0], 0.8 * p["C"][1]]
+    T = _run(probe, tmp_path, p, div=1, uf=2.0)
+    S = make_setup(p, div_correction=1, ushort_factor=2.0)
+    for mode, (wrt, s0) in enumerate((("A", 0), ("A", 1), ("C", 0), ("C", 1))):
+        ks = KN.JastrowKernels(S.A, S.C, deriv=(wrt, s0))
+        D = dict(T["deriv"][mode], did=T["did"], delta=T["delta"])
+        _compare_tables(D, S, ks)
+        for s in range(2):
+            ref = ks.corr(s, S.Gamma0, S.ushort_factor, S.Nk)
+            assert abs(D["corr"][s] - ref) <= 1e-12 * max(abs(ref), 1e-30), (mode, s, D["corr"][s], ref)
+            assert D["amp"][s] == ks.amp(s), (mode, s)
+    assert abs(T["gsq0"] - KN.gradu_sq(np.array([0.0]), S.A[0], S.C[0])[0]) <= 1e-15 * abs(T["gsq0"])
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_layout_and_band_constants_match_the_oracle(probe, tmp_path, name):
+    """Sphere sizes, Miller vectors (lexicographic, zero padded) and box indices (-1 padded) of every
+    k-point, and Gamma_b and W at an off-mesh k, against the oracle (oracle/cell.py, oracle/band.py)."""
+    p = CASES[name]()
+    T = _run(probe, tmp_path, p)
+    S = make_setup(p)
+    assert T["npw_max"] == S.npw_max and T["npw"].tolist() == S.npw.tolist()
+    n = S.n[0]
+    for k in range(S.Nk):
+        m = S.npw[k]
+        assert np.array_equal(T["miller"][k, :m], S.miller[k])
+        assert not T["miller"][k, m:].any() and np.all(T["box"][k, m:] == -1)
+        i0, i1, i2 = S.box_index[k]
+        assert np.array_equal(T["box"][k, :m], (i0 * n + i1) * n + i2)
+    kc = np.array([0.13, 0.27, -0.31]) @ S.B
+    assert T["band"]["found"]
+    gb = BD.gamma_band(S.lattice, S.kmesh, S.alpha, kc)
+    W = BD.aux_vector_sum(S.lattice, S.kmesh, S.alpha, kc)
+    assert abs(T["band"]["gamma_b"] - gb) <= 1e-12 * abs(gb)
+    np.testing.assert_allclose(T["band"]["W"], W, rtol=0, atol=1e-12 * np.abs(W).max())
+
+
+def test_host_sphere_cutoff_and_box_fit(probe, tmp_path):
+    """On the simple-cubic cell of edge 2 pi at Gamma (b_i = unit vectors exactly) the sphere of
+    E_cut = r2/2 holds the integer vectors with |m|^2 <= r2 (cumulative sums of r3(n); a wave on the
+    cutoff belongs to the sphere), and a sphere that reaches Miller index n/2 of an even box (which the
+    box index n/2 cannot tell from -n/2) is refused."""
+    counts = {1: 7, 2: 19, 3: 27, 5: 57, 9: 123, 25: 515}
+    base = dict(lattice=2.0 * np.pi * np.eye(3), kmesh=(1, 1, 1), fft=(12,) * 3, nbands=1, nocc=1,
+                A=[1.0, 1.0], C=[1.0, 1.0])
+    for r2, want in counts.items():
+        T = _run(probe, tmp_path, dict(base, ecut=0.5 * r2))
+        assert T["npw"].tolist() == [want], r2
+    out = str(tmp_path / "refused.bin")
+    p = dict(base, ecut=0.5 * 36)      # |m| = 6 = n/2 on the axes
+    args = [probe, out] + ["%.17g" % x for x in np.asarray(p["lattice"]).ravel()] + ["1", "1", "1"]
+    args += ["%.17g" % p["ecut"], "12", "1", "1", "1", "1", "1", "1", "0", "1", "1"]
+    r = subprocess.run(args, capture_output=True, text=True)
+    assert r.returncode == 1 and "does not fit" in r.stderr
