@@ -160,10 +160,19 @@ def _near_mesh(div, deltas, general=False, m=1):
     e /= np.linalg.norm(e)
     out = []
     for d in deltas:
-        kb = S.kfrac[m] + d * e
+        # the point next to k_m, and a second band point far from the mesh whose outputs must not
+        # depend on the first (its own Gamma_b, W and orbitals)
+        kb = np.stack([S.kfrac[m] + d * e, K_OFF])
         SB = BD.BandSetup(S, kb)
         assert np.array_equal(SB.miller[S.Nk], S.miller[m])
-        out.append(BD.band_apply(S, c_phi, c_chi, occ, kb, c_phi[m:m + 1], c_chi[m:m + 1], occ[m:m + 1]))
+        bp, bc = synth.random_orbitals(synth.SEED0 + 64, [SB.kpG(S.Nk + 1)], SB.npw_max, S.nbands, perturb=0.2)
+        n0 = S.npw[m]
+        b_phi = np.zeros((2, S.nbands, SB.npw_max), complex)
+        b_chi = np.zeros_like(b_phi)
+        b_phi[0, :, :n0], b_chi[0, :, :n0] = c_phi[m, :, :n0], c_chi[m, :, :n0]
+        b_phi[1], b_chi[1] = bp[0], bc[0]
+        b_occ = np.stack([occ[m], occ[m]])
+        out.append(BD.band_apply(S, c_phi, c_chi, occ, kb, b_phi, b_chi, b_occ))
     return out
 
 
@@ -178,12 +187,14 @@ def test_band_corrections_cancel_the_singularity_next_to_a_mesh_point(general):
     A_ap) leaves a divergent remainder."""
     near = _near_mesh(1, (1e-3, 1e-4), general)
     bare = _near_mesh(0, (1e-3, 1e-4), general)
-    scale = max(np.abs(near[0][t]).max() for t in OP.TERMS)
+    scale = max(np.abs(near[0][t][0]).max() for t in OP.TERMS)
     for t in OP.TERMS:
-        a, b = near[0][t], near[1][t]
+        a, b = near[0][t][0], near[1][t][0]
         assert np.abs(b - a).max() <= 0.02 * max(np.abs(a).max(), 1e-3 * scale), t
+        far = np.abs(near[0][t][1]).max()
+        assert np.abs(near[1][t][1] - near[0][t][1]).max() <= 1e-12 * max(far, scale), t   # the far point
     for t in ("2ax", "2bx1", "2bx2", "3a3", "3a4", "3b3", "3b4", "3b5", "3b6"):
-        assert np.abs(bare[1][t]).max() > 5.0 * np.abs(bare[0][t]).max(), t      # the singular terms are there
+        assert np.abs(bare[1][t][0]).max() > 5.0 * np.abs(bare[0][t][0]).max(), t  # the singular terms are there
 
 
 def _heg_band_case(kmesh=(2, 2, 1), nbands=9, A=None):

@@ -66,6 +66,17 @@ def test_sphere_cutoff_is_inclusive():
         assert len(CL.sphere_miller(np.zeros(3), B, 0.5 * r2)) == want, r2
 
 
+def test_alpha_reading_on_the_fcc_supercell():
+    """sqrt(alpha) = L_min/12 with L_min the shortest vector of the Born-von Karman supercell: for the
+    fcc cell (|a_i| = a/sqrt 2) on an n x n x n mesh that is n a/sqrt 2 (the supercell is the fcc cell
+    scaled by n), on a 4 x 2 x 1 mesh the shortest of 4 a_1, 2 a_2, a_3 and their combinations, a/sqrt 2."""
+    lat = synth.si_params()["lattice"]
+    a = 10.26
+    for n in (1, 2, 4):
+        assert abs(CL.default_alpha(lat, (n, n, n)) - (n * a / np.sqrt(2.0) / 12.0) ** 2) < 1e-12
+    assert abs(CL.default_alpha(lat, (4, 2, 1)) - (a / np.sqrt(2.0) / 12.0) ** 2) < 1e-12
+
+
 def test_kmesh_and_box_conventions():
     f = CL.kmesh_frac((4, 1, 3))
     assert f.shape == (12, 3)

@@ -41,6 +41,39 @@ def test_point_groups():
             np.testing.assert_allclose(Sc @ Sc.T, np.eye(3), atol=1e-12)
 
 
+def test_cartesian_forms_on_a_non_symmetric_basis():
+    """x -> S x on fractional coordinates is r -> L^T S L^-T r in Cartesian ones (rows a_i of L): the
+    Cartesian form of every operation that keeps the metric is orthogonal, also for a basis whose matrix
+    is not symmetric (the fcc cell with a_3 replaced by a_1 + a_3), and a proper rotation for det S = 1."""
+    L = np.array([[1, 0, 0], [0, 1, 0], [1, 0, 1]]) @ synth.si_params()["lattice"]
+    assert np.abs(L - L.T).max() > 1.0
+    Sset = type("Cell", (), {"lattice": L})()
+    ops = synth.point_group(L, atoms_frac=((0.0, 0.0, 0.0),))
+    assert len(ops) >= 8
+    for S in ops:
+        R = SY.cart(Sset, S)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert abs(np.linalg.det(R) - np.linalg.det(S)) < 1e-12
+        np.testing.assert_allclose(R @ L.T, L.T @ S, atol=1e-12)      # maps the rotated lattice vectors
+
+
+def test_kmap_takes_the_first_operation_in_order():
+    """Each irreducible point is its own image under the identity (operation 0, no time reversal, K = 0),
+    and every other point records the first operation, in the stated order (all operations without time
+    reversal, then all with it), that reaches it from its irreducible point."""
+    p = synth.si_params(kmesh=(4, 4, 4))
+    S = make_setup(p)
+    ops = synth.point_group(p["lattice"])
+    kinfo, irred = SY.kmap(ops, S.kfrac, True)
+    for k0 in irred:
+        assert kinfo[k0][0] == k0 and kinfo[k0][1] == 0 and kinfo[k0][2] == 1 and not np.any(kinfo[k0][3])
+    order = [(tr, s) for tr in (1, -1) for s in range(len(ops))]
+    for k, (k0, s, tr, K) in enumerate(kinfo):
+        for tr2, s2 in order[: order.index((tr, s))]:
+            d = tr2 * (ops[s2].T @ S.kfrac[k0]) - S.kfrac[k]
+            assert not np.all(np.abs(d - np.round(d)) < 1e-9), (k, tr2, s2)
+
+
 @pytest.mark.parametrize("kmesh,nirr", [((4, 4, 4), 8), ((2, 2, 2), 3), ((3, 3, 3), 4)])
 def test_irreducible_k_points(kmesh, nirr):
     """T_d with time reversal acts on k like O_h (time reversal supplies the inversion): the same
