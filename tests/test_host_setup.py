@@ -191,3 +191,38 @@ def test_host_sphere_cutoff_and_box_fit(probe, tmp_path):
     args += ["%.17g" % p["ecut"], "12", "1", "1", "1", "1", "1", "1", "0", "1", "1"]
     r = subprocess.run(args, capture_output=True, text=True)
     assert r.returncode == 1 and "does not fit" in r.stderr
+
+
+def _refused(probe, tmp_path, p, **kw):
+    args = [probe, str(tmp_path / "refused.bin")] + ["%.17g" % x for x in np.asarray(p["lattice"]).ravel()]
+    args += [str(k) for k in p["kmesh"]] + ["%.17g" % p["ecut"], str(p["fft"][0]), str(p["nbands"]), str(p["nocc"])]
+    args += ["%.17g" % x for x in p["A"]] + ["%.17g" % x for x in p["C"]] + ["0", "1", "1"]
+    r = subprocess.run(args, capture_output=True, text=True)
+    return r.returncode, r.stderr.strip()
+
+
+@pytest.mark.parametrize("change,message", [
+    (dict(fft=(10, 10, 10)), "unsupported: FFT box size"),
+    (dict(kmesh=(0, 1, 1)), "kmesh entries must be in [1, 16]"),
+    (dict(kmesh=(17, 1, 1)), "kmesh entries must be in [1, 16]"),
+    (dict(nocc=0), "need 0 < nocc <= nbands"),
+    (dict(nocc=4, nbands=3), "need 0 < nocc <= nbands"),
+    (dict(ecut=0.0), "ecut_ha must be positive"),
+    (dict(C=[1.0, 0.0]), "Jastrow C must be positive"),
+    (dict(A=[-0.1, 1.0]), "Jastrow A must be non-negative"),
+    (dict(lattice=np.zeros((3, 3))), "lattice is singular"),
+    (dict(ecut=40.0), "plane-wave sphere does not fit the FFT box"),
+])
+def test_host_setup_refuses_invalid_parameters(probe, tmp_path, change, message):
+    """The argument checks of tc_init's host setup, each with its message (and nothing built)."""
+    p = dict(synth.tiny_params(3, kmesh=(1, 1, 2), fft=(9, 9, 9), ecut=1.6, scale=5.0), **change)
+    rc, err = _refused(probe, tmp_path, p)
+    assert rc == 1 and err.startswith(message), (rc, err)
+
+
+def test_host_setup_accepts_the_limits(probe, tmp_path):
+    """The edges of the accepted ranges: A = 0 (the Hartree-Fock limit), nocc = nbands, a 16-point mesh axis."""
+    p = dict(synth.tiny_params(3, kmesh=(16, 1, 1), fft=(9, 9, 9), ecut=1.6, scale=5.0), A=[0.0, 0.0])
+    p["nocc"] = p["nbands"]
+    T = _run(probe, tmp_path, p)
+    assert T["Nk"] == 16
